@@ -1,0 +1,254 @@
+/*
+ * Plain FP64 CPU oracle of the iterative Sherman-Morrison EnKF analysis
+ * (Nino-Ruiz, Sandu and Anderson, "An Efficient Implementation of the Ensemble
+ * Kalman Filter Based on an Iterative Sherman-Morrison Formula").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  The CUDA library shares no code,
+ * header or constant with it, and neither links the other.
+ *
+ * Every routine follows the paper's definition step by step, in double
+ * precision, with no blocking, fusion or reordering beyond what the paper
+ * writes.  Sums over observations run in ascending row order.  Parallelism is
+ * only over independent columns (or state rows), so the result does not depend
+ * on the thread count.  Compile with -fno-fast-math -ffp-contract=off.
+ *
+ * Storage: column-major, one ensemble member per column, leading dimension ld.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Ensemble statistics and observation space (Sec. 2 and Sec. 3)           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Ensemble mean and deviations, eq. (ensemble-background-mean):
+ *   xbar = X_B 1 / Nens,   dX_B[:, e] = X_B[:, e] - xbar.
+ * The paper's S (eq. EnSM:Matrix-member-deviations) is dX_B / sqrt(Nens - 1).
+ */
+void oracle_ensemble_deviations(int64_t nstate, int32_t nens, const double* XB, int64_t ldb,
+                                double* xbar, double* dXB, int64_t ldx) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nstate; ++i) {
+        double s = 0.0;
+        for (int32_t e = 0; e < nens; ++e) s += XB[e * ldb + i];
+        double m = s / (double)nens;
+        if (xbar) xbar[i] = m;
+        for (int32_t e = 0; e < nens; ++e) dXB[e * ldx + i] = XB[e * ldb + i] - m;
+    }
+}
+
+/*
+ * Observation-space ensemble deviations, eq. (EnKSM:member-observations):
+ *   V = H S = H dX_B / sqrt(Nens - 1),
+ * with H selecting state rows 0, stride, 2*stride, ... (nobs rows).
+ */
+void oracle_observe_deviations(int64_t nobs, int32_t nens, int32_t stride, const double* dXB, int64_t ldx,
+                               double* V, int64_t ldv) {
+    double scale = 1.0 / sqrt((double)(nens - 1));
+#pragma omp parallel for schedule(static)
+    for (int32_t e = 0; e < nens; ++e)
+        for (int64_t j = 0; j < nobs; ++j) V[e * ldv + j] = dXB[e * ldx + j * (int64_t)stride] * scale;
+}
+
+/*
+ * Innovations, eq. (EnKSM:system-rhs):  D = Y - H X_B.
+ */
+void oracle_innovations(int64_t nobs, int32_t nens, int32_t stride, const double* Y, int64_t ldy,
+                        const double* XB, int64_t ldb, double* D, int64_t ldd) {
+#pragma omp parallel for schedule(static)
+    for (int32_t e = 0; e < nens; ++e)
+        for (int64_t j = 0; j < nobs; ++j) D[e * ldd + j] = Y[e * ldy + j] - XB[e * ldb + j * (int64_t)stride];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iterative Sherman-Morrison formula S_*(R, V, D), Sec. 3.1               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Step 1, eq. (SM-step-1):  Z^(0) = R^{-1} D,  U^(0) = R^{-1} V,  R = diag(r).
+ * Each row j is divided by r_j.  nrhs is the number of columns of D
+ * (Nens in the paper).  Adds nobs * (nens + nrhs) long operations (one
+ * division per entry; 2 Nobs Nens when nrhs = Nens, eq.
+ * EnKSM:operations-count-step-one) to *longops when longops is not NULL.
+ */
+void oracle_ism_step1(int64_t nobs, int32_t nens, int32_t nrhs, const double* r,
+                      const double* V, int64_t ldv, const double* D, int64_t ldd,
+                      double* U, int64_t ldu, double* Z, int64_t ldz, int64_t* longops) {
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < nrhs; ++i)
+        for (int64_t j = 0; j < nobs; ++j) Z[i * ldz + j] = D[i * ldd + j] / r[j];
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < nens; ++i)
+        for (int64_t j = 0; j < nobs; ++j) U[i * ldu + j] = V[i * ldv + j] / r[j];
+    if (longops) *longops += (int64_t)nobs * (nens + nrhs);
+}
+
+/* v^T x over rows 0..nobs-1, ascending. */
+static double dot_asc(int64_t nobs, const double* v, const double* x) {
+    double s = 0.0;
+    for (int64_t j = 0; j < nobs; ++j) s += v[j] * x[j];
+    return s;
+}
+
+/*
+ * Step 2, eqs. (SM-step-2-h), (SM-step-2-Z), (SM-step-2-u): for levels
+ * k = 1..Nens (0-based k = 0..Nens-1 here):
+ *   gamma_k = 1 + v_k^T u_k^(k-1)
+ *   h_k     = u_k^(k-1) / gamma_k
+ *   Z^(k)   = Z^(k-1) - h_k (v_k^T Z^(k-1))                 (every column of Z)
+ *   u_i^(k) = u_i^(k-1) - h_k (v_k^T u_i^(k-1)),  i > k     (later columns of U only)
+ * Column u_k is not touched at level k or after (Sec. 3.1: at iteration k only
+ * columns k < i <= Nens are updated).  All three lines read level-(k-1) data.
+ *
+ * gamma (length nens) receives gamma_k when not NULL.  Long operations (products
+ * and divisions, as counted in Sec. 3.2) are added to *longops when not NULL.
+ * Returns 0, or k+1 when gamma_k is not finite or not positive (the level at
+ * which the recurrence cannot proceed, Sec. 3.3).
+ */
+int oracle_ism_step2(int64_t nobs, int32_t nens, int32_t nrhs, const double* V, int64_t ldv,
+                     double* U, int64_t ldu, double* Z, int64_t ldz, double* gamma, int64_t* longops) {
+    double* h = (double*)malloc(sizeof(double) * (size_t)(nobs > 0 ? nobs : 1));
+    if (!h) return -1;
+    int status = 0;
+    for (int32_t k = 0; k < nens; ++k) {
+        const double* vk = V + k * ldv;
+        const double* uk = U + k * ldu;
+        double g = 1.0 + dot_asc(nobs, vk, uk);
+        if (gamma) gamma[k] = g;
+        if (!(g > 0.0) || !isfinite(g)) { status = k + 1; break; }
+        for (int64_t j = 0; j < nobs; ++j) h[j] = uk[j] / g;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t i = 0; i < nrhs; ++i) {
+            double* z = Z + i * ldz;
+            double c = dot_asc(nobs, vk, z);
+            for (int64_t j = 0; j < nobs; ++j) z[j] -= h[j] * c;
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t i = k + 1; i < nens; ++i) {
+            double* u = U + i * ldu;
+            double c = dot_asc(nobs, vk, u);
+            for (int64_t j = 0; j < nobs; ++j) u[j] -= h[j] * c;
+        }
+        if (longops) *longops += 2 * nobs + 2 * nobs * (int64_t)nrhs + 2 * nobs * (int64_t)(nens - 1 - k);
+    }
+    free(h);
+    return status;
+}
+
+/*
+ * S_*(R, V, D): Step 1 then Step 2.  U is caller-provided scratch (nobs x nens).
+ */
+int oracle_ism_solve(int64_t nobs, int32_t nens, int32_t nrhs, const double* r,
+                     const double* V, int64_t ldv, const double* D, int64_t ldd,
+                     double* U, int64_t ldu, double* Z, int64_t ldz, double* gamma, int64_t* longops) {
+    oracle_ism_step1(nobs, nens, nrhs, r, V, ldv, D, ldd, U, ldu, Z, ldz, longops);
+    return oracle_ism_step2(nobs, nens, nrhs, V, ldv, U, ldu, Z, ldz, gamma, longops);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Analysis assembly, Sec. 3.1 (SMEnKF)                                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * M = V^T Z / sqrt(Nens - 1)  (nens x nrhs, column-major, ld = nens), so that
+ * S V^T Z = dX_B M with S = dX_B / sqrt(Nens - 1).
+ */
+void oracle_vtz(int64_t nobs, int32_t nens, int32_t nrhs, const double* V, int64_t ldv,
+                const double* Z, int64_t ldz, double* M) {
+    double scale = 1.0 / sqrt((double)(nens - 1));
+#pragma omp parallel for schedule(static) collapse(2)
+    for (int32_t i = 0; i < nrhs; ++i)
+        for (int32_t m = 0; m < nens; ++m) M[i * nens + m] = dot_asc(nobs, V + m * ldv, Z + i * ldz) * scale;
+}
+
+/*
+ * X_A = X_B + S V^T Z = X_B + dX_B M  (SMEnKF analysis, Sec. 3.1).  The sum over
+ * ensemble members runs in ascending order.  XA may alias XB.
+ */
+void oracle_analysis_update(int64_t nstate, int32_t nens, int32_t nrhs, const double* XB, int64_t ldb,
+                            const double* dXB, int64_t ldx, const double* M, double* XA, int64_t lda) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nstate; ++i) {
+        for (int32_t e = 0; e < nrhs; ++e) {
+            double s = 0.0;
+            for (int32_t m = 0; m < nens; ++m) s += dXB[m * ldx + i] * M[e * nens + m];
+            XA[e * lda + i] = XB[e * ldb + i] + s;
+        }
+    }
+}
+
+/*
+ * Residual of the analysis linear system, eq. (EnKSM:system-to-solve-V):
+ *   Res = D - (R + V V^T) Z = D - (r o Z + V (V^T Z)).
+ * P = V^T Z is formed first (nens x nrhs), then each entry of Res.
+ */
+int oracle_residual(int64_t nobs, int32_t nens, int32_t nrhs, const double* r, const double* V, int64_t ldv,
+                    const double* D, int64_t ldd, const double* Z, int64_t ldz, double* Res, int64_t ldr) {
+    double* P = (double*)malloc(sizeof(double) * (size_t)nens * (size_t)(nrhs > 0 ? nrhs : 1));
+    if (!P) return -1;
+#pragma omp parallel for schedule(static) collapse(2)
+    for (int32_t i = 0; i < nrhs; ++i)
+        for (int32_t m = 0; m < nens; ++m) P[i * nens + m] = dot_asc(nobs, V + m * ldv, Z + i * ldz);
+#pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < nrhs; ++i) {
+        for (int64_t j = 0; j < nobs; ++j) {
+            double s = 0.0;
+            for (int32_t m = 0; m < nens; ++m) s += V[m * ldv + j] * P[i * nens + m];
+            Res[i * ldr + j] = D[i * ldd + j] - (r[j] * Z[i * ldz + j] + s);
+        }
+    }
+    free(P);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lorenz-96 forecast model, Sec. 4.2 eq. (eqn:Lorenz96), integrated by RK4 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * dx_i/dt = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F with periodic indices
+ * (0-based here; the paper writes the wrap-around cases i = 1 and i = Nstate
+ * explicitly).
+ */
+void oracle_l96_rhs(int64_t n, const double* x, double F, double* dx) {
+    for (int64_t i = 0; i < n; ++i) {
+        double xp1 = x[(i + 1) % n];
+        double xm1 = x[(i - 1 + n) % n];
+        double xm2 = x[(i - 2 + 2 * n) % n];
+        dx[i] = (xp1 - xm2) * xm1 - x[i] + F;
+    }
+}
+
+/*
+ * Classical fourth-order Runge-Kutta, nsteps steps of size dt, applied to every
+ * ensemble member (column) of X independently:
+ *   k1 = f(x), k2 = f(x + dt/2 k1), k3 = f(x + dt/2 k2), k4 = f(x + dt k3),
+ *   x <- x + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ */
+int oracle_l96_rk4(int64_t nstate, int32_t nens, double* X, int64_t ld, double F, double dt, int32_t nsteps) {
+    int status = 0;
+#pragma omp parallel for schedule(static)
+    for (int32_t e = 0; e < nens; ++e) {
+        double* x = X + e * ld;
+        double* w = (double*)malloc(sizeof(double) * (size_t)nstate * 5);
+        if (!w) { status = -1; continue; }
+        double *k1 = w, *k2 = w + nstate, *k3 = w + 2 * nstate, *k4 = w + 3 * nstate, *t = w + 4 * nstate;
+        for (int32_t s = 0; s < nsteps; ++s) {
+            oracle_l96_rhs(nstate, x, F, k1);
+            for (int64_t i = 0; i < nstate; ++i) t[i] = x[i] + 0.5 * dt * k1[i];
+            oracle_l96_rhs(nstate, t, F, k2);
+            for (int64_t i = 0; i < nstate; ++i) t[i] = x[i] + 0.5 * dt * k2[i];
+            oracle_l96_rhs(nstate, t, F, k3);
+            for (int64_t i = 0; i < nstate; ++i) t[i] = x[i] + dt * k3[i];
+            oracle_l96_rhs(nstate, t, F, k4);
+            for (int64_t i = 0; i < nstate; ++i)
+                x[i] = x[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+        }
+        free(w);
+    }
+    return status;
+}
