@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the iterative Sherman-Morrison EnKF analysis on one GB300.
+
+Workload (default): the large single analysis -- Nstate = 2^21, Nobs = 2^19
+(every 4th state variable observed), Nens = 128; deviations dX_B[i,e] = s_i N(0,1)
+with s_i ~ U[0.5, 2], variances r_j ~ U[0.5, 1.5], innovations D ~ N(0,1), and the
+background equal to the deviations.  One step = the whole analysis through the C
+ABI: V = H dX_B / sqrt(Nens-1) on the device, Step 1 + Step 2 of the iterative
+Sherman-Morrison formula, M = V^T Z / sqrt(Nens-1), X_A = X_B + dX_B M.  Inputs
+(1.3 GB) are larger than L2, so no flush is needed between steps.
+
+The headline path is the FP32 plain level-streaming path; the FP64 plain path
+is timed in the same run as the comparator.  ``--impl reference`` times the
+FP64 CPU oracle instead (bounded sample of the same workload).
+
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "analyses/s"
+NSTATE, NOBS, NENS, STRIDE = 1 << 21, 1 << 19, 128, 4
+WORKLOAD = f"large_single Nstate={NSTATE} Nobs={NOBS} Nens={NENS} (every {STRIDE}th variable observed)"
+
+
+def flops(nstate, nobs, nens):
+    """Flop convention: F_solve = 6 Nobs Nens^2 + 3 Nobs Nens (Sec. 3.2 counts, a
+    multiply-add = 2), F_M = 2 Nobs Nens^2, F_XA = 2 Nstate Nens^2 + Nstate Nens."""
+    return 6 * nobs * nens ** 2 + 3 * nobs * nens + 2 * nobs * nens ** 2 + 2 * nstate * nens ** 2 + nstate * nens
+
+
+def level_bytes(nobs, nens, w):
+    """Algorithmic bytes of the level-streaming kernel per launch: Step 1 reads D, V
+    and writes Z, U (4 N Nobs); level k reads and writes its 2N-1-k active columns
+    and reads u_k and v_{k+1} (2 columns); summed: w Nobs (3 N^2 + 5 N)."""
+    return w * nobs * (3 * nens * nens + 5 * nens)
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_src: str, workload_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current source of the kernel (sha256 recorded in the summary)."""
+    path = os.path.join(ROOT, "profiles", f"ism_levels_{workload_key}.md")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+        m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if m_sha and m_tr and m_sha.group(1) == sha:
+            return float(m_tr.group(1))
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                mhz.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(frac_log2: int, seconds: float, seed_offset: int = 0):
+    """Times the FP64 oracle on a row sample of the workload: Nobs and Nstate divided
+    by 2^frac_log2, Nens unchanged (cost is linear in Nobs and Nstate)."""
+    import numpy as np
+    import oracle
+    import synth
+    nobs, nstate = NOBS >> frac_log2, NSTATE >> frac_log2
+    w = synth.large_single(nstate, nobs, NENS, dtype=np.float64)
+    dXB, r, D = w["dXB"], w["r"], w["D"]
+    oracle.build()
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        V = oracle.observe_deviations(dXB, nobs, STRIDE)
+        oracle.analysis(r, V, D, dXB, dXB)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    per_run = el / runs
+    return {
+        "value": (1.0 / per_run) / (1 << frac_log2),
+        "unit": METRIC,
+        "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+        "kind": "oracle",
+        "sample": f"Nobs={nobs}, Nstate={nstate}, Nens={NENS} (1/{1 << frac_log2} of the rows), {runs} run(s) "
+                  f"in {el:.1f} s; analyses/s scaled by 1/{1 << frac_log2}",
+        "seconds_per_sample": per_run,
+    }
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(3, 0.0)
+    sample = None
+    for _ in range(args.steps):
+        sample = cpu_oracle_sample(3, 0.0)
+        per_step.append(sample["seconds_per_sample"] * 8)
+    value = args.steps / sum(per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "1/8 of the rows per step, time scaled by 8"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": sample["cores"], "kind": "oracle",
+                         "sample": sample["sample"]},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+
+    # cpu baseline first (rank 0, before any large device allocation)
+    cpu = cpu_oracle_sample(3, args.cpu_seconds) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = synth.large_single(NSTATE, NOBS, NENS, dtype=np.float32)
+    h_dX = torch.from_numpy(w["dXB"]).pin_memory()
+    h_D = torch.from_numpy(w["D"]).pin_memory()
+    h_r = torch.from_numpy(w["r"]).pin_memory()
+    dX = h_dX.to(dev)
+    D = h_D.to(dev)
+    r = h_r.to(dev)
+    V = torch.empty(NENS, NOBS, dtype=torch.float32, device=dev)
+    XA = torch.empty_like(dX)
+    M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
+    plan = enkf.Plan(NSTATE, NOBS, NENS, enkf.ENKF_FP32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.obs_prep(STRIDE, 0, None, dX, V)
+        plan.analysis(r, V, D, dXB=dX, XB=dX, XA=XA, M=M)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    inf = plan.analysis(r, V, D, dXB=dX, XB=dX, XA=XA, M=M, info=True)   # status check, untimed
+    enkf.enkf_ism_profile(plan.handle, True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    phases = enkf.enkf_ism_profile_read(plan.handle)
+    enkf.enkf_ism_profile(plan.handle, False)
+    t_max = t_ms
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # end to end through the API with host buffers: H2D of the inputs, the analysis, D2H of X_A
+    h_XA = torch.empty(XA.shape, dtype=XA.dtype).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        dX.copy_(h_dX, non_blocking=True)
+        D.copy_(h_D, non_blocking=True)
+        r.copy_(h_r, non_blocking=True)
+        step()
+        h_XA.copy_(XA, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = h_dX.numel() * 4 + h_D.numel() * 4 + h_r.numel() * 4
+    d2h = h_XA.numel() * 4
+
+    # plain FP64 comparator on the same values (fewer steps: it is FP64-ALU bound)
+    fp64 = None
+    if not args.no_fp64:
+        del h_XA
+        dX64 = dX.double()
+        D64 = D.double()
+        r64 = r.double()
+        V64 = torch.empty(NENS, NOBS, dtype=torch.float64, device=dev)
+        XA64 = torch.empty_like(dX64)
+        M64 = torch.empty(NENS * NENS, dtype=torch.float64, device=dev)
+        plan64 = enkf.Plan(NSTATE, NOBS, NENS, enkf.ENKF_FP64, device=dev)
+
+        def step64():
+            plan64.obs_prep(STRIDE, 0, None, dX64, V64)
+            plan64.analysis(r64, V64, D64, dXB=dX64, XB=dX64, XA=XA64, M=M64)
+
+        step64()
+        barrier()
+        k64 = max(1, min(args.steps, 3))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k64):
+            step64()
+        f1.record(stream)
+        barrier()
+        ms64 = f0.elapsed_time(f1) / k64
+        # accuracy of the FP32 path against the FP64 path on X_A (same inputs)
+        err_xa = float(torch.linalg.norm(XA.double() - XA64) / torch.linalg.norm(XA64))
+        err_inc = float(torch.linalg.norm((XA.double() - dX64) - (XA64 - dX64)) / torch.linalg.norm(XA64 - dX64))
+        err_m = float(torch.linalg.norm(M.double() - M64) / torch.linalg.norm(M64))
+        fp64 = {"path": "plain FP64 level-streaming", "ms_per_step": ms64, "analyses_per_s": 1e3 / ms64,
+                "speedup_fp32_over_fp64": ms64 / (t_max / args.steps),
+                "fp32_rel_err_vs_fp64": {"XA": err_xa, "increment": err_inc, "M": err_m}}
+        plan64.close()
+
+    if rank != 0:
+        return
+    peak, peak_kind = read_peaks()
+    lv_ms, lv_n = phases.get("ism_levels", (float("nan"), 0))
+    lv_avg = lv_ms / max(lv_n, 1)
+    lb = level_bytes(NOBS, NENS, 4)
+    achieved = lb / (lv_avg / 1e3) / 1e9
+    total_ms = sum(v[0] for v in phases.values())
+    ms_step = t_max / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nstate": NSTATE, "nobs": NOBS, "nens": NENS,
+                   "path": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)",
+                   "l2": "inputs 1.3 GB > L2; no flush", "parallelism": f"replicas x{world}"},
+        "gflops": flops(NSTATE, NOBS, NENS) / (ms_step / 1e3) / 1e9,
+        "gamma_min": inf.gamma_min, "gamma_max": inf.gamma_max,
+        "roofline": {"kernel": "ism_levels_kernel<float,4>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
+                     "traffic": profile_traffic(os.path.join(ROOT, "paper_1302_3876_gb300", "csrc", "ism_stream.cu"),
+                                                "large_single_fp32")},
+        "phases_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in phases.items()},
+        "phase_share": {k: v[0] / total_ms for k, v in phases.items()} if total_ms > 0 else {},
+        "e2e": {"value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk.summary(),
+        "comparator_fp64": fp64,
+        "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * enkf_ism.h -- C ABI of the GB300 (sm_103a) iterative Sherman-Morrison EnKF
+ * analysis library (libenkf_ism.so).
+ *
+ * The method is the one of Nino-Ruiz, Sandu and Anderson, "An Efficient
+ * Implementation of the Ensemble Kalman Filter Based on an Iterative
+ * Sherman-Morrison Formula" (Statistics and Computing, 2014):
+ *
+ *   D   = Y - H X_B                                    (Sec. 3, eq. EnKSM:system-rhs)
+ *   V   = H S,  S = (X_B - xbar 1^T) / sqrt(Nens - 1)  (eqs. EnSM:Matrix-member-deviations,
+ *                                                        EnKSM:member-observations)
+ *   Z   = S_*(R, V, D) = (R + V V^T)^{-1} D            (Sec. 3.1, Steps 1 and 2, eqs.
+ *                                                        SM-step-1, SM-step-2-h/Z/u)
+ *   X_A = X_B + S V^T Z = X_B + dX_B M,
+ *   M   = V^T Z / sqrt(Nens - 1)                       (Sec. 3.1, SMEnKF analysis)
+ *
+ * with R = diag(r) (r holds observation-error VARIANCES, r_j > 0).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major, one ensemble member per column, with a leading
+ *   dimension ld >= rows.  Only rows [0, rows) of each column are read or
+ *   written; padding rows are never touched.
+ * - Every array argument is a DEVICE pointer owned by the caller (for example
+ *   a torch tensor's data_ptr()).  The library never allocates or frees device
+ *   memory on the analysis path: scratch space is the caller's workspace, sized
+ *   by enkf_ism_plan().  The one exception is enkf_ism_plan() itself, which
+ *   allocates nothing on the device either (it only queries device properties).
+ * - Element type follows the plan's mode: ENKF_FP64 means every floating-point
+ *   buffer is double; every other mode uses float storage.
+ * - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *   void*; NULL is the legacy default stream).  Device-side checks (r_j <= 0,
+ *   non-finite values, gamma_k < 1 - tol, an expired bounded wait) latch a status
+ *   word in the workspace; it is returned by the next call on the same plan, or
+ *   immediately when a non-NULL info pointer is given (which synchronises the
+ *   stream).
+ * - Errors are return codes only: no exit(), no abort(), no device trap.  After
+ *   ENKF_ERR_CUDA the detail text is in enkf_last_error().
+ * - Pointers passed to one call must not overlap unless stated (X_A may alias
+ *   X_B).
+ */
+#ifndef ENKF_ISM_H
+#define ENKF_ISM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ENKF_API __attribute__((visibility("default")))
+#else
+#define ENKF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ENKF_OK = 0,
+    ENKF_ERR_ARG = 1,         /* NULL where a pointer is required, bad enum or flag, bad alignment */
+    ENKF_ERR_SHAPE = 2,       /* a size or leading dimension out of range */
+    ENKF_ERR_CUDA = 3,        /* a CUDA runtime call failed (see enkf_last_error) */
+    ENKF_ERR_NUMERIC = 4,     /* r_j <= 0, a non-finite value, or gamma_k < 1 - tol (Sec. 3.3) */
+    ENKF_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    ENKF_ERR_UNSUPPORTED = 6, /* mode / size combination this build does not implement */
+    ENKF_ERR_WORKSPACE = 7    /* workspace NULL, too small or not 256-byte aligned */
+} enkf_status;
+
+typedef enum {
+    ENKF_FP64 = 0,        /* plain level-by-level path, double storage and arithmetic */
+    ENKF_FP32 = 1,        /* plain level-by-level path, float storage, double gamma */
+    ENKF_PANEL_BF16 = 2,  /* panel form, bf16 tensor-core trailing updates, FP64 denominators */
+    ENKF_PANEL_FP16 = 3   /* panel form, fp16 tensor-core trailing updates, FP64 denominators */
+} enkf_mode;
+
+/* Plan flags. */
+#define ENKF_FLAG_REFINE        0x1u  /* panel modes: one iterative-refinement sweep of Z */
+#define ENKF_FLAG_NO_CHECKS     0x2u  /* skip the device-side gamma / finiteness checks */
+#define ENKF_FLAG_TEST_TIMEOUT  0x4u  /* test only: one CTA skips its first grid-barrier arrival,
+                                         so the others' bounded wait expires (ENKF_ERR_TIMEOUT) */
+
+typedef struct enkf_ism_plan_s* enkf_ism_plan_t;  /* opaque plan handle, host-owned */
+
+/* Diagnostics filled by enkf_ism_analysis when info != NULL (forces a stream sync). */
+typedef struct {
+    double gamma_min;      /* min_k gamma_k = 1 + v_k^T u_k^(k-1)  (Theorem 2: > 1) */
+    double gamma_max;      /* max_k gamma_k */
+    int32_t panel_b;       /* panel width used (0 for the plain path) */
+    int32_t grid_ctas;     /* CTAs of the level-streaming launch */
+    int32_t status;        /* device status word of this call */
+    int32_t reserved;
+} enkf_ism_info;
+
+/*
+ * enkf_ism_plan -- validate sizes and choose launch shapes for one problem size.
+ *
+ *   out              receives the plan (host object; free with enkf_ism_plan_destroy).
+ *   nstate           state dimension (rows of X_B, dX_B, X_A); >= 1.
+ *   nobs             number of observations (rows of V, D, Z); >= 1.
+ *   nens             ensemble size (columns); 1 <= nens <= 1024.  nens = 1 allows
+ *                    the solve only (M and X_A need nens >= 2, since S divides
+ *                    by sqrt(Nens - 1)).
+ *   mode             an enkf_mode.
+ *   panel_b          panel width for the panel modes (0 = default); ignored otherwise.
+ *   flags            ENKF_FLAG_* bits.
+ *   workspace_bytes  receives the device workspace size enkf_ism_analysis needs.
+ *
+ * Uses the CUDA device current on the calling thread.  Returns ENKF_ERR_SHAPE
+ * for out-of-range sizes, ENKF_ERR_UNSUPPORTED for an unimplemented mode.
+ */
+ENKF_API enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, int32_t nens,
+                          int32_t mode, int32_t panel_b, uint32_t flags, size_t* workspace_bytes);
+
+ENKF_API void enkf_ism_plan_destroy(enkf_ism_plan_t plan);
+
+/*
+ * enkf_obs_prep -- observation-space preparation (Sec. 2 eq. ensemble-background-mean,
+ * Sec. 3 eqs. EnSM:Matrix-member-deviations, EnKSM:member-observations,
+ * EnKSM:system-rhs), with H selecting state rows 0, obs_stride, 2 obs_stride, ...
+ *
+ *   center = 1: dX_B = X_B - xbar 1^T is computed from X_B (written to dXB).
+ *   center = 0: dXB is an input (deviations given); XB may be NULL when Y is NULL.
+ *   Always:     V = H dX_B / sqrt(Nens - 1)           (nobs x nens, written to V).
+ *   Y != NULL:  D = Y - H X_B                          (nobs x nens, written to D).
+ *
+ * Requires (nobs - 1) * obs_stride < nstate and nens >= 2.  Sizes come from the plan.
+ */
+ENKF_API enkf_status enkf_obs_prep(enkf_ism_plan_t plan, int32_t obs_stride, int32_t center,
+                          const void* XB, int64_t ldb,
+                          void* dXB, int64_t ldx,
+                          const void* Y, int64_t ldy,
+                          void* V, int64_t ldv,
+                          void* D, int64_t ldd,
+                          void* stream);
+
+/*
+ * enkf_ism_analysis -- one EnKF analysis by the iterative Sherman-Morrison formula.
+ *
+ *   r     [nobs]         observation-error variances (R = diag(r)), all > 0.
+ *   V     nobs x nens    observation-space deviations, ld ldv.
+ *   D     nobs x nens    innovations, ld ldd.
+ *   dXB   nstate x nens  background deviations, ld ldx; NULL computes Z (and M) only.
+ *   XB    nstate x nens  background ensemble, ld ldb (ignored when dXB is NULL).
+ *   XA    nstate x nens  analysis ensemble (output), ld lda; may alias XB (then ldb == lda).
+ *   Z     nobs x nens    solution of (R + V V^T) Z = D (output, nullable), ld ldz.
+ *   M     nens x nens    V^T Z / sqrt(Nens - 1) (output, nullable), column-major, ld nens.
+ *   workspace            device scratch of at least the plan's workspace_bytes,
+ *                        256-byte aligned; owned by the caller, reused across calls,
+ *                        not shared by calls in flight at the same time.
+ *   stream               cudaStream_t to run on.
+ *   info                 host pointer or NULL; when given, the call synchronises the
+ *                        stream and fills it.
+ *
+ * Every array is read-only except XA, Z, M and the workspace.  Z and M are
+ * written only when non-NULL.  Returns ENKF_ERR_NUMERIC / ENKF_ERR_TIMEOUT from
+ * the device status word (immediately with info, else at the next call).
+ */
+ENKF_API enkf_status enkf_ism_analysis(enkf_ism_plan_t plan,
+                              const void* r,
+                              const void* V, int64_t ldv,
+                              const void* D, int64_t ldd,
+                              const void* dXB, int64_t ldx,
+                              const void* XB, int64_t ldb,
+                              void* XA, int64_t lda,
+                              void* Z, int64_t ldz,
+                              void* M,
+                              void* workspace, size_t workspace_bytes,
+                              void* stream, enkf_ism_info* info);
+
+/*
+ * Kernel-phase timing (tracing aid).  enkf_ism_profile(plan, 1) makes every later
+ * enkf_obs_prep / enkf_ism_analysis call on the plan record CUDA events around
+ * each of its kernel phases on the caller's stream (up to 4096 phases between
+ * reads).  enkf_ism_profile_read synchronises on the last recorded event, adds
+ * the elapsed milliseconds of each phase into ms[phase] and the number of
+ * launches into count[phase] (arrays of ENKF_PROFILE_PHASES, caller-owned host
+ * memory), and clears the record.  Phases: 0 obs prep, 1 level streaming (Step 1
+ * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update.
+ */
+#define ENKF_PROFILE_PHASES 8
+ENKF_API enkf_status enkf_ism_profile(enkf_ism_plan_t plan, int32_t enable);
+ENKF_API enkf_status enkf_ism_profile_read(enkf_ism_plan_t plan, double* ms, int32_t* count);
+
+/* Human-readable name of a status code (static string). */
+ENKF_API const char* enkf_status_string(enkf_status s);
+
+/* Detail text of the last error raised on the calling thread (thread-local). */
+ENKF_API const char* enkf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENKF_ISM_H */

@@ -1,0 +1,359 @@
+// C ABI of libenkf_ism (declared in include/enkf_ism.h): plans, argument
+// validation, workspace layout and the orchestration of one analysis.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/enkf_ism.h"
+#include "internal.h"
+
+using namespace enkf;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+enkf_status fail(enkf_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+enkf_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(ENKF_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                  \
+    do {                                                \
+        cudaError_t e__ = (call);                       \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t pad32(int64_t x) { return (x + 31) / 32 * 32; }
+
+}  // namespace
+
+struct enkf_ism_plan_s {
+    int64_t nstate, nobs;
+    int32_t nens, mode, panel_b;
+    uint32_t flags;
+    int device;
+    bool fp64;
+    size_t w;                 // element size
+    LevelLaunch L;
+    int32_t nsplit;
+    int64_t ldu, ldzw;
+    // workspace layout (byte offsets)
+    size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, total;
+    // latched status of the previous call
+    int* h_status;            // pinned host word
+    cudaEvent_t done;
+    bool pending;
+    // kernel-phase timing
+    bool prof;
+    int nprof;
+    cudaEvent_t* prof_ev;     // [2 * kProfCap]
+    int* prof_phase;          // [kProfCap]
+};
+
+namespace {
+constexpr int kProfCap = 4096;
+
+// Records the start event of a phase; returns the slot or -1.
+int prof_begin(enkf_ism_plan_s* p, int phase, cudaStream_t s) {
+    if (!p->prof || p->nprof >= kProfCap) return -1;
+    const int i = p->nprof++;
+    p->prof_phase[i] = phase;
+    cudaEventRecord(p->prof_ev[2 * i], s);
+    return i;
+}
+
+void prof_end(enkf_ism_plan_s* p, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(p->prof_ev[2 * slot + 1], s);
+}
+}  // namespace
+
+extern "C" {
+
+const char* enkf_status_string(enkf_status s) {
+    switch (s) {
+        case ENKF_OK: return "ENKF_OK";
+        case ENKF_ERR_ARG: return "ENKF_ERR_ARG";
+        case ENKF_ERR_SHAPE: return "ENKF_ERR_SHAPE";
+        case ENKF_ERR_CUDA: return "ENKF_ERR_CUDA";
+        case ENKF_ERR_NUMERIC: return "ENKF_ERR_NUMERIC";
+        case ENKF_ERR_TIMEOUT: return "ENKF_ERR_TIMEOUT";
+        case ENKF_ERR_UNSUPPORTED: return "ENKF_ERR_UNSUPPORTED";
+        case ENKF_ERR_WORKSPACE: return "ENKF_ERR_WORKSPACE";
+    }
+    return "ENKF_UNKNOWN_STATUS";
+}
+
+const char* enkf_last_error(void) { return g_last_error; }
+
+enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, int32_t nens, int32_t mode,
+                          int32_t panel_b, uint32_t flags, size_t* workspace_bytes) {
+    if (!out || !workspace_bytes) return fail(ENKF_ERR_ARG, "enkf_ism_plan: NULL out or workspace_bytes");
+    *out = nullptr;
+    if (nstate < 1 || nobs < 1 || nens < 1)
+        return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: need nstate, nobs, nens >= 1 (got %lld, %lld, %d)",
+                    (long long)nstate, (long long)nobs, nens);
+    if (nens > 1024) return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: nens %d > 1024", nens);
+    if (nobs > ((int64_t)1 << 40) || nstate > ((int64_t)1 << 40))
+        return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: size too large");
+    if (mode != ENKF_FP64 && mode != ENKF_FP32) {
+        if (mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16)
+            return fail(ENKF_ERR_UNSUPPORTED, "enkf_ism_plan: panel modes are not built yet");
+        return fail(ENKF_ERR_ARG, "enkf_ism_plan: bad mode %d", mode);
+    }
+    if (flags & ~(ENKF_FLAG_REFINE | ENKF_FLAG_NO_CHECKS | ENKF_FLAG_TEST_TIMEOUT))
+        return fail(ENKF_ERR_ARG, "enkf_ism_plan: unknown flag bits 0x%x", flags);
+    enkf_ism_plan_s* p = new (std::nothrow) enkf_ism_plan_s();
+    if (!p) return fail(ENKF_ERR_ARG, "enkf_ism_plan: out of host memory");
+    p->nstate = nstate;
+    p->nobs = nobs;
+    p->nens = nens;
+    p->mode = mode;
+    p->panel_b = 0;
+    p->flags = flags;
+    p->fp64 = (mode == ENKF_FP64);
+    p->w = p->fp64 ? 8 : 4;
+    (void)panel_b;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = level_plan(p->fp64, nobs, nens, &p->L);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "enkf_ism_plan: level_plan");
+    }
+    p->nsplit = gram_upper_nsplit(nobs, nens);
+    p->ldu = pad32(nobs);
+    p->ldzw = pad32(nobs);
+    const size_t N = (size_t)nens;
+    size_t o = 0;
+    p->off_ctl = o; o = align256(o + sizeof(Control));
+    p->off_U = o; o = align256(o + p->w * (size_t)p->ldu * N);
+    p->off_Z = o; o = align256(o + p->w * (size_t)p->ldzw * N);
+    p->off_part = o; o = align256(o + sizeof(double) * (size_t)p->L.grid * 2 * N);
+    p->off_coefg = o; o = align256(o + sizeof(double) * 2 * N);
+    p->off_C = o; o = align256(o + sizeof(double) * N * N);
+    p->off_gamma = o; o = align256(o + sizeof(double) * N);
+    p->off_Qpart = o; o = align256(o + sizeof(double) * (size_t)p->nsplit * N * N);
+    p->off_Q = o; o = align256(o + sizeof(double) * N * N);
+    p->off_M = o; o = align256(o + p->w * N * N);
+    p->off_M64 = o; o = align256(o + sizeof(double) * N * N);
+    p->total = o;
+    e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (p->h_status) cudaFreeHost(p->h_status);
+        delete p;
+        return cuda_fail(e, "enkf_ism_plan: host status");
+    }
+    *p->h_status = 0;
+    p->pending = false;
+    *workspace_bytes = p->total;
+    *out = p;
+    return ENKF_OK;
+}
+
+void enkf_ism_plan_destroy(enkf_ism_plan_t p) {
+    if (!p) return;
+    if (p->pending) cudaEventSynchronize(p->done);
+    cudaEventDestroy(p->done);
+    cudaFreeHost(p->h_status);
+    if (p->prof_ev) {
+        for (int i = 0; i < 2 * kProfCap; ++i) cudaEventDestroy(p->prof_ev[i]);
+        free(p->prof_ev);
+        free(p->prof_phase);
+    }
+    delete p;
+}
+
+enkf_status enkf_ism_profile(enkf_ism_plan_t p, int32_t enable) {
+    if (!p) return fail(ENKF_ERR_ARG, "enkf_ism_profile: NULL plan");
+    if (enable && !p->prof_ev) {
+        p->prof_ev = (cudaEvent_t*)calloc(2 * kProfCap, sizeof(cudaEvent_t));
+        p->prof_phase = (int*)calloc(kProfCap, sizeof(int));
+        if (!p->prof_ev || !p->prof_phase) return fail(ENKF_ERR_ARG, "enkf_ism_profile: out of host memory");
+        for (int i = 0; i < 2 * kProfCap; ++i) CU(cudaEventCreate(&p->prof_ev[i]), "cudaEventCreate");
+    }
+    p->prof = enable != 0;
+    p->nprof = 0;
+    return ENKF_OK;
+}
+
+enkf_status enkf_ism_profile_read(enkf_ism_plan_t p, double* ms, int32_t* count) {
+    if (!p || !ms || !count) return fail(ENKF_ERR_ARG, "enkf_ism_profile_read: NULL argument");
+    if (p->nprof > 0) CU(cudaEventSynchronize(p->prof_ev[2 * (p->nprof - 1) + 1]), "cudaEventSynchronize");
+    for (int i = 0; i < p->nprof; ++i) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, p->prof_ev[2 * i], p->prof_ev[2 * i + 1]), "cudaEventElapsedTime");
+        const int ph = p->prof_phase[i];
+        if (ph >= 0 && ph < ENKF_PROFILE_PHASES) {
+            ms[ph] += (double)t;
+            count[ph] += 1;
+        }
+    }
+    p->nprof = 0;
+    return ENKF_OK;
+}
+
+static enkf_status take_latched(enkf_ism_plan_t p) {
+    if (!p->pending) return ENKF_OK;
+    if (cudaEventQuery(p->done) != cudaSuccess) return ENKF_OK;   // not finished yet: checked later
+    p->pending = false;
+    const int st = *p->h_status;
+    *p->h_status = 0;
+    if (st != 0) return fail((enkf_status)st, "device status of a previous call: %s", enkf_status_string((enkf_status)st));
+    return ENKF_OK;
+}
+
+static bool ld_ok(int64_t ld, int64_t rows) { return ld >= rows && ld >= 1; }
+
+enkf_status enkf_obs_prep(enkf_ism_plan_t p, int32_t obs_stride, int32_t center, const void* XB, int64_t ldb, void* dXB,
+                          int64_t ldx, const void* Y, int64_t ldy, void* V, int64_t ldv, void* D, int64_t ldd,
+                          void* stream) {
+    if (!p) return fail(ENKF_ERR_ARG, "enkf_obs_prep: NULL plan");
+    if (obs_stride < 1) return fail(ENKF_ERR_SHAPE, "enkf_obs_prep: obs_stride %d < 1", obs_stride);
+    if ((p->nobs - 1) * (int64_t)obs_stride >= p->nstate)
+        return fail(ENKF_ERR_SHAPE, "enkf_obs_prep: (nobs-1)*stride >= nstate");
+    if (p->nens < 2) return fail(ENKF_ERR_SHAPE, "enkf_obs_prep: nens must be >= 2");
+    if (!dXB || !V) return fail(ENKF_ERR_ARG, "enkf_obs_prep: NULL dXB or V");
+    if ((center || Y) && !XB) return fail(ENKF_ERR_ARG, "enkf_obs_prep: XB required");
+    if (Y && !D) return fail(ENKF_ERR_ARG, "enkf_obs_prep: D required with Y");
+    if (!ld_ok(ldx, p->nstate) || !ld_ok(ldv, p->nobs) || ((center || Y) && !ld_ok(ldb, p->nstate)) ||
+        (Y && (!ld_ok(ldy, p->nobs) || !ld_ok(ldd, p->nobs))))
+        return fail(ENKF_ERR_SHAPE, "enkf_obs_prep: leading dimension smaller than rows");
+    CU(cudaSetDevice(p->device), "cudaSetDevice");
+    const int slot = prof_begin(p, 0, (cudaStream_t)stream);
+    CU(obs_prep(p->fp64, p->nstate, p->nobs, p->nens, obs_stride, center, XB, ldb, dXB, ldx, Y, ldy, V, ldv, D, ldd,
+                (cudaStream_t)stream),
+       "enkf_obs_prep launch");
+    prof_end(p, slot, (cudaStream_t)stream);
+    return ENKF_OK;
+}
+
+enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, int64_t ldv, const void* D, int64_t ldd,
+                              const void* dXB, int64_t ldx, const void* XB, int64_t ldb, void* XA, int64_t lda, void* Z,
+                              int64_t ldz, void* M, void* workspace, size_t workspace_bytes, void* stream,
+                              enkf_ism_info* info) {
+    if (!p) return fail(ENKF_ERR_ARG, "enkf_ism_analysis: NULL plan");
+    if (!r || !V || !D) return fail(ENKF_ERR_ARG, "enkf_ism_analysis: NULL r, V or D");
+    if (!ld_ok(ldv, p->nobs) || !ld_ok(ldd, p->nobs) || (Z && !ld_ok(ldz, p->nobs)))
+        return fail(ENKF_ERR_SHAPE, "enkf_ism_analysis: ldv/ldd/ldz smaller than nobs");
+    if (dXB) {
+        if (!XB || !XA) return fail(ENKF_ERR_ARG, "enkf_ism_analysis: XB and XA required with dXB");
+        if (!ld_ok(ldx, p->nstate) || !ld_ok(ldb, p->nstate) || !ld_ok(lda, p->nstate))
+            return fail(ENKF_ERR_SHAPE, "enkf_ism_analysis: ldx/ldb/lda smaller than nstate");
+        if (XA == XB && lda != ldb) return fail(ENKF_ERR_ARG, "enkf_ism_analysis: XA aliases XB with lda != ldb");
+    }
+    if ((dXB || M) && p->nens < 2)
+        return fail(ENKF_ERR_SHAPE, "enkf_ism_analysis: M and X_A need nens >= 2 (S divides by sqrt(Nens-1))");
+    if (!workspace || workspace_bytes < p->total)
+        return fail(ENKF_ERR_WORKSPACE, "enkf_ism_analysis: workspace %zu bytes < required %zu", workspace_bytes,
+                    p->total);
+    if ((uintptr_t)workspace % 256 != 0) return fail(ENKF_ERR_WORKSPACE, "enkf_ism_analysis: workspace not 256-aligned");
+    const uintptr_t wmask = p->w - 1;
+    if (((uintptr_t)r | (uintptr_t)V | (uintptr_t)D | (uintptr_t)dXB | (uintptr_t)XB | (uintptr_t)XA | (uintptr_t)Z |
+         (uintptr_t)M) & wmask)
+        return fail(ENKF_ERR_ARG, "enkf_ism_analysis: pointer not aligned to the element size");
+
+    enkf_status latched = take_latched(p);
+    if (latched != ENKF_OK) return latched;
+
+    CU(cudaSetDevice(p->device), "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    Control* ctl = (Control*)(ws + p->off_ctl);
+    CU(cudaMemsetAsync(ctl, 0, sizeof(Control), s), "cudaMemsetAsync(control)");
+
+    void* Zp = Z ? Z : (void*)(ws + p->off_Z);
+    const int64_t ldzp = Z ? ldz : p->ldzw;
+    LevelArgs a;
+    a.nobs = p->nobs;
+    a.nens = p->nens;
+    a.r = r;
+    a.V = V;
+    a.ldv = ldv;
+    a.D = D;
+    a.ldd = ldd;
+    a.U = ws + p->off_U;
+    a.ldu = p->ldu;
+    a.Z = Zp;
+    a.ldz = ldzp;
+    a.part = (double*)(ws + p->off_part);
+    a.coefg = (double*)(ws + p->off_coefg);
+    a.C = (double*)(ws + p->off_C);
+    a.gamma = (double*)(ws + p->off_gamma);
+    a.ctl = ctl;
+    a.rows_per_blk = p->L.rows_per_blk;
+    a.rows_chunk = p->L.rows_chunk;
+    a.check = (p->flags & ENKF_FLAG_NO_CHECKS) ? 0 : 1;
+    a.test_skip_arrival = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 1 : 0;
+    a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
+    int slot = prof_begin(p, 1, s);
+    CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
+    prof_end(p, slot, s);
+
+    if (M || dXB) {
+        double* Q = (double*)(ws + p->off_Q);
+        slot = prof_begin(p, 2, s);
+        CU(gram_upper(p->fp64, p->nobs, p->nens, V, ldv, a.U, p->ldu, (double*)(ws + p->off_Qpart), p->nsplit, Q, s),
+           "gram launch");
+        prof_end(p, slot, s);
+        void* Mp = M ? M : (void*)(ws + p->off_M);
+        slot = prof_begin(p, 3, s);
+        CU(assemble_M(p->fp64, p->nens, Q, a.C, a.gamma, Mp, (double*)(ws + p->off_M64), s), "assemble_M launch");
+        prof_end(p, slot, s);
+        if (dXB) {
+            slot = prof_begin(p, 4, s);
+            CU(xa_update(p->fp64, p->nstate, p->nens, XB, ldb, dXB, ldx, Mp, XA, lda, s), "xa_update launch");
+            prof_end(p, slot, s);
+        }
+    }
+    CU(cudaMemcpyAsync(p->h_status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
+    CU(cudaEventRecord(p->done, s), "cudaEventRecord");
+    p->pending = true;
+
+    if (info) {
+        CU(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        p->pending = false;
+        const int st = *p->h_status;
+        *p->h_status = 0;
+        memset(info, 0, sizeof(*info));
+        info->status = st;
+        info->grid_ctas = p->L.grid;
+        info->panel_b = 0;
+        double* g = (double*)malloc(sizeof(double) * (size_t)p->nens);
+        if (!g) return fail(ENKF_ERR_ARG, "out of host memory");
+        cudaError_t e = cudaMemcpy(g, a.gamma, sizeof(double) * (size_t)p->nens, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            free(g);
+            return cuda_fail(e, "gamma copy");
+        }
+        double gmin = INFINITY, gmax = -INFINITY;
+        for (int k = 0; k < p->nens; ++k) {
+            gmin = fmin(gmin, g[k]);
+            gmax = fmax(gmax, g[k]);
+        }
+        free(g);
+        info->gamma_min = gmin;
+        info->gamma_max = gmax;
+        if (st != 0) {
+            Control hc;
+            cudaMemcpy(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+            return fail((enkf_status)st, "device status %s (level %d)", enkf_status_string((enkf_status)st),
+                        hc.fail_level);
+        }
+    }
+    return ENKF_OK;
+}
+
+}  // extern "C"

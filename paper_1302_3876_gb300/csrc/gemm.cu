@@ -1,0 +1,242 @@
+// Analysis assembly of the SMEnKF (Sec. 3.1): M = V^T Z / sqrt(Nens - 1) and
+// X_A = X_B + dX_B M.
+//
+// M is assembled from the recurrence's own quantities rather than from a direct
+// product V^T Z, which cancels catastrophically when gamma_k >> 1 (the part of Z
+// in range(V) is damped by 1/gamma and dominated by rounding).  From eqs.
+// SM-step-2-Z, for k < m:  v_k^T Z^(m) = v_k^T Z^(m-1) - (v_k^T h_m) c_m, and
+// v_k^T Z^(k) = c_k / gamma_k, so with Q_km = v_k^T u_m^(m-1) (the final, frozen
+// columns of U) and chat_m = c_m / gamma_m:
+//     V^T Z = (I - triu(Q, 1)) chat,
+// an identity in exact arithmetic.  Q is a strictly-upper Gram matrix of V and the
+// final U, computed here split over rows with double partials.
+#include <math.h>
+
+#include "internal.h"
+
+namespace enkf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Q[k][m] = sum_j A[j,k] B[j,m], k < m.  64 x 64 output tile per CTA, 256 threads
+// with 4 x 4 outputs each, rows in sub-blocks of 32 staged transposed in smem.
+// ---------------------------------------------------------------------------
+constexpr int GT = 64;   // tile edge
+constexpr int GR = 32;   // rows per smem stage
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_upper_kernel(int64_t nrows, int n, const T* __restrict__ A, int64_t lda,
+                                                         const T* __restrict__ B, int64_t ldb, int64_t rows_per_split,
+                                                         double* __restrict__ Qpart) {
+    __shared__ T As[GT][GR + 1];
+    __shared__ T Bs[GT][GR + 1];
+    // map blockIdx.x to an upper tile (kb <= mb)
+    const int nt = (n + GT - 1) / GT;
+    int t = blockIdx.x, kb = 0;
+    while (t >= nt - kb) {
+        t -= nt - kb;
+        ++kb;
+    }
+    const int mb = kb + t;
+    const int split = blockIdx.y;
+    const int64_t j0 = (int64_t)split * rows_per_split;
+    const int64_t j1 = min(j0 + rows_per_split, nrows);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double accd[4][4];
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) accd[i][q] = 0.0, acc[i][q] = T(0);
+    int stage = 0;
+    for (int64_t jb = j0; jb < j1; jb += GR) {
+        __syncthreads();
+        // load 32 rows x 64 columns of A and B: lane -> row, warp and step -> column
+        const int lr = tid & 31;
+        for (int c = tid >> 5; c < GT; c += 8) {
+            const int64_t j = jb + lr;
+            const int ka = kb * GT + c, mbc = mb * GT + c;
+            As[c][lr] = (j < j1 && ka < n) ? A[(int64_t)ka * lda + j] : T(0);
+            Bs[c][lr] = (j < j1 && mbc < n) ? B[(int64_t)mbc * ldb + j] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int j = 0; j < GR; ++j) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Bs[tx * 4 + q][j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] += a[i] * b[q];
+        }
+        // fold the working-precision accumulators into double every 16 stages (512 rows)
+        if (++stage == 16) {
+            stage = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) accd[i][q] += (double)acc[i][q], acc[i][q] = T(0);
+        }
+    }
+    double* out = Qpart + (int64_t)split * n * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = kb * GT + ty * 4 + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int m = mb * GT + tx * 4 + q;
+            if (k < n && m < n && k < m) out[(int64_t)k * n + m] = accd[i][q] + (double)acc[i][q];
+        }
+    }
+}
+
+__global__ void gram_reduce_kernel(int n, int nsplit, const double* __restrict__ Qpart, double* __restrict__ Q) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), m = (int)(e % n);
+        double s = 0.0;
+        if (k < m)
+            for (int p = 0; p < nsplit; ++p) s += Qpart[(int64_t)p * nn + e];
+        Q[e] = s;
+    }
+}
+
+// M[k + i n] = (chat[k][i] - sum_{m>k} Q[k][m] chat[m][i]) / sqrt(n - 1), chat[m][i] = C[m][i] / gamma_m.
+template <typename T>
+__global__ void assemble_M_kernel(int n, const double* __restrict__ Q, const double* __restrict__ C,
+                                  const double* __restrict__ gamma, T* __restrict__ M, double* __restrict__ M64) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * n) return;
+    const int k = (int)(e % n), i = (int)(e / n);
+    double s = C[(int64_t)k * n + i] / gamma[k];
+    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] / gamma[m]);
+    s *= 1.0 / sqrt((double)(n - 1));
+    if (M) M[e] = (T)s;
+    if (M64) M64[e] = s;
+}
+
+// ---------------------------------------------------------------------------
+// XA = XB + dXB * M.  CTA tile 128 rows x 64 columns, 256 threads; lane -> 4 rows
+// (lane + 32 r), warp -> 8 columns.  The 64 needed columns of M sit in smem for
+// the whole K = n; dXB is staged 32 columns (of K) at a time.
+// ---------------------------------------------------------------------------
+constexpr int XBM = 128, XBN = 64, XBK = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) xa_update_kernel(int64_t nstate, int n, const T* XB, int64_t ldb,
+                                                        const T* __restrict__ dXB, int64_t ldx,
+                                                        const T* __restrict__ M, T* XA, int64_t lda) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ms = reinterpret_cast<T*>(smem_raw);          // [n][XBN]  Ms[k*XBN + c] = M[k + (e0+c) n]
+    T* As = Ms + (size_t)n * XBN;                    // [XBK][XBM]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * XBM;
+    const int e0 = blockIdx.y * XBN;
+    for (int idx = tid; idx < n * XBN; idx += 256) {
+        const int k = idx / XBN, c = idx % XBN;
+        Ms[idx] = (e0 + c < n) ? M[k + (int64_t)(e0 + c) * n] : T(0);
+    }
+    T acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
+    for (int k0 = 0; k0 < n; k0 += XBK) {
+        __syncthreads();
+        for (int idx = tid; idx < XBK * XBM; idx += 256) {
+            const int kk = idx / XBM, rr = idx % XBM;
+            const int64_t i = i0 + rr;
+            As[idx] = (k0 + kk < n && i < nstate) ? dXB[(int64_t)(k0 + kk) * ldx + i] : T(0);
+        }
+        __syncthreads();
+        const int kmax = min(XBK, n - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            T a[4], b[8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk * XBM + lane + 32 * r];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) b[c] = Ms[(k0 + kk) * XBN + warp * 8 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] += a[r] * b[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int e = e0 + warp * 8 + c;
+        if (e >= n) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t i = i0 + lane + 32 * r;
+            if (i < nstate) XA[(int64_t)e * lda + i] = XB[(int64_t)e * ldb + i] + acc[r][c];
+        }
+    }
+}
+
+}  // namespace
+
+int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
+    const int nt = (n + GT - 1) / GT;
+    const int tiles = nt * (nt + 1) / 2;
+    int64_t want = (152 * 4 + tiles - 1) / tiles;          // about four waves of CTAs
+    int64_t by_rows = (nrows + 1023) / 1024;               // at least 1024 rows per split
+    int64_t s = want < by_rows ? want : by_rows;
+    if (s < 1) s = 1;
+    if (s > 1024) s = 1024;
+    return (int32_t)s;
+}
+
+cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
+    const int nt = (n + GT - 1) / GT;
+    const int tiles = nt * (nt + 1) / 2;
+    int64_t rps = (nrows + nsplit - 1) / nsplit;
+    rps = (rps + GR - 1) / GR * GR;
+    dim3 grid(tiles, nsplit);
+    if (fp64)
+        gram_upper_kernel<double><<<grid, 256, 0, s>>>(nrows, n, (const double*)A, lda, (const double*)B, ldb, rps, Qpart);
+    else
+        gram_upper_kernel<float><<<grid, 256, 0, s>>>(nrows, n, (const float*)A, lda, (const float*)B, ldb, rps, Qpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nn = (int64_t)n * n;
+    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, nsplit, Qpart, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C, const double* gamma, void* M,
+                       double* M64, cudaStream_t s) {
+    const int64_t nn = (int64_t)nens * nens;
+    const int blocks = (int)((nn + 255) / 256);
+    if (fp64)
+        assemble_M_kernel<double><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (double*)M, M64);
+    else
+        assemble_M_kernel<float><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (float*)M, M64);
+    return cudaGetLastError();
+}
+
+cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, int64_t ldb, const void* dXB,
+                      int64_t ldx, const void* M, void* XA, int64_t lda, cudaStream_t s) {
+    const size_t w = fp64 ? 8 : 4;
+    const size_t smem = w * ((size_t)nens * XBN + (size_t)XBK * XBM);
+    dim3 grid((unsigned)((nstate + XBM - 1) / XBM), (unsigned)((nens + XBN - 1) / XBN));
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(xa_update_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        xa_update_kernel<double><<<grid, 256, smem, s>>>(nstate, nens, (const double*)XB, ldb, (const double*)dXB, ldx,
+                                                         (const double*)M, (double*)XA, lda);
+    } else {
+        e = cudaFuncSetAttribute(xa_update_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        xa_update_kernel<float><<<grid, 256, smem, s>>>(nstate, nens, (const float*)XB, ldb, (const float*)dXB, ldx,
+                                                        (const float*)M, (float*)XA, lda);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace enkf

@@ -1,0 +1,68 @@
+// Internal launcher interfaces between the translation units of libenkf_ism.
+// Host code only; no torch types, no exceptions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace enkf {
+
+// Plain level-streaming solve (Step 1 + Step 2 of the iterative Sherman-Morrison
+// formula) for one problem.
+struct LevelArgs {
+    int64_t nobs;
+    int32_t nens;
+    const void* r;
+    const void* V; int64_t ldv;
+    const void* D; int64_t ldd;
+    void* U; int64_t ldu;          // workspace, nobs x nens
+    void* Z; int64_t ldz;          // output, nobs x nens
+    double* part;                  // [grid][2*nens] per-CTA partial dots
+    double* coefg;                 // [2*nens] reduced coefficients of the current level
+    double* C;                     // [nens][nens] Z coefficients c_{k,i} = v_k^T Z^(k-1)[:,i]
+    double* gamma;                 // [nens]
+    Control* ctl;
+    int32_t rows_per_blk;          // rows owned by one CTA (multiple of the vector width)
+    int32_t rows_chunk;            // rows staged in shared memory at a time
+    int32_t check;                 // run the numeric checks
+    int32_t test_skip_arrival;     // test-only: CTA 0 leaves before its first arrival
+    uint64_t timeout_ns;
+};
+
+struct LevelLaunch {
+    int grid;
+    int threads;
+    size_t smem;
+    int rows_per_blk;
+    int rows_chunk;
+    int vec;
+};
+
+// Chooses the launch shape for (nobs, nens) on the current device.
+cudaError_t level_plan(bool fp64, int64_t nobs, int32_t nens, LevelLaunch* out);
+cudaError_t level_launch(bool fp64, const LevelLaunch& L, LevelArgs a, cudaStream_t s);
+
+// Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,
+// partials in double; then Q = sum of the partials in a fixed order.
+cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
+                       int64_t ldb, double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
+int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
+
+// M = (I - triu(Q,1)) diag(1/gamma) C / sqrt(nens - 1)  (nens x nens, column-major
+// output in T: M[m + e*nens]).  C is [level][column].
+cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C, const double* gamma,
+                       void* M, double* M64, cudaStream_t s);
+
+// XA = XB + dXB * M  (nstate x nens, K = nens); XA may alias XB.
+cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, int64_t ldb,
+                      const void* dXB, int64_t ldx, const void* M, void* XA, int64_t lda, cudaStream_t s);
+
+// Observation-space preparation.
+cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int32_t stride, int32_t center,
+                     const void* XB, int64_t ldb, void* dXB, int64_t ldx, const void* Y, int64_t ldy,
+                     void* V, int64_t ldv, void* D, int64_t ldd, cudaStream_t s);
+
+}  // namespace enkf

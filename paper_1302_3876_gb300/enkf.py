@@ -1,0 +1,230 @@
+"""Thin Python binding of libenkf_ism (C ABI in include/enkf_ism.h).
+
+Argument marshalling only: every step of the analysis runs in the library's
+CUDA kernels.  Functions carry the C names.  Array arguments are CUDA torch
+tensors laid out column-major: a matrix with ``rows`` rows and ``cols`` columns
+is a tensor of shape ``(cols, rows)`` (or a ``[:, :rows]`` view of a padded
+``(cols, ld)`` tensor) whose leading dimension is ``tensor.stride(0)``.
+
+There is no fallback: if the shared library is missing or fails to load, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+ENKF_OK = 0
+ENKF_ERR_ARG = 1
+ENKF_ERR_SHAPE = 2
+ENKF_ERR_CUDA = 3
+ENKF_ERR_NUMERIC = 4
+ENKF_ERR_TIMEOUT = 5
+ENKF_ERR_UNSUPPORTED = 6
+ENKF_ERR_WORKSPACE = 7
+
+ENKF_FP64 = 0
+ENKF_FP32 = 1
+ENKF_PANEL_BF16 = 2
+ENKF_PANEL_FP16 = 3
+
+ENKF_FLAG_REFINE = 0x1
+ENKF_FLAG_NO_CHECKS = 0x2
+ENKF_FLAG_TEST_TIMEOUT = 0x4
+
+ENKF_PROFILE_PHASES = 8
+PROFILE_PHASE_NAMES = ("obs_prep", "ism_levels", "gram_upper", "assemble_M", "xa_update", "", "", "")
+
+
+class EnkfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+class enkf_ism_info(ctypes.Structure):
+    _fields_ = [("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double), ("panel_b", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load libenkf_ism.so (raises if it is missing and building is not requested)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libenkf_ism.so not built ({path}); run paper_1302_3876_gb300.build.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        i64, i32, u32, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+        lib.enkf_ism_plan.argtypes = [ctypes.POINTER(vp), i64, i64, i32, i32, i32, u32, ctypes.POINTER(sz)]
+        lib.enkf_ism_plan.restype = ctypes.c_int
+        lib.enkf_ism_plan_destroy.argtypes = [vp]
+        lib.enkf_ism_plan_destroy.restype = None
+        lib.enkf_obs_prep.argtypes = [vp, i32, i32, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp]
+        lib.enkf_obs_prep.restype = ctypes.c_int
+        lib.enkf_ism_analysis.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, sz,
+                                          vp, ctypes.POINTER(enkf_ism_info)]
+        lib.enkf_ism_analysis.restype = ctypes.c_int
+        lib.enkf_ism_profile.argtypes = [vp, i32]
+        lib.enkf_ism_profile.restype = ctypes.c_int
+        lib.enkf_ism_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.enkf_ism_profile_read.restype = ctypes.c_int
+        lib.enkf_status_string.argtypes = [ctypes.c_int]
+        lib.enkf_status_string.restype = ctypes.c_char_p
+        lib.enkf_last_error.argtypes = []
+        lib.enkf_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    try:
+        return load().enkf_status_string(status).decode()
+    except Exception:  # noqa: BLE001 - used while formatting another error
+        return f"status {status}"
+
+
+def _check(status: int):
+    if status != ENKF_OK:
+        raise EnkfError(status, load().enkf_last_error().decode())
+
+
+def _mat(t, name):
+    """(pointer, ld) of a column-major matrix tensor of shape (cols, rows)."""
+    if t is None:
+        return None, 0
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() == 1:
+        return ctypes.c_void_p(t.data_ptr()), max(t.shape[0], 1)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D tensor with unit row stride (shape (cols, rows))")
+    return ctypes.c_void_p(t.data_ptr()), int(t.stride(0)) if t.shape[0] > 1 else int(max(t.stride(0), t.shape[1]))
+
+
+def _ptr(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def enkf_ism_plan(nstate: int, nobs: int, nens: int, mode: int, panel_b: int = 0, flags: int = 0):
+    """Returns (plan handle, workspace bytes)."""
+    lib = load()
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check(lib.enkf_ism_plan(ctypes.byref(h), nstate, nobs, nens, mode, panel_b, flags, ctypes.byref(ws)))
+    return h, ws.value
+
+
+def enkf_ism_plan_destroy(plan) -> None:
+    load().enkf_ism_plan_destroy(plan)
+
+
+def enkf_obs_prep(plan, obs_stride: int, center: int, XB, dXB, V, Y=None, D=None, stream=None) -> None:
+    pXB, ldb = _mat(XB, "XB")
+    pdX, ldx = _mat(dXB, "dXB")
+    pY, ldy = _mat(Y, "Y")
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    _check(load().enkf_obs_prep(plan, obs_stride, center, pXB, ldb, pdX, ldx, pY, ldy, pV, ldv, pD, ldd,
+                                _stream(stream)))
+
+
+def enkf_ism_analysis(plan, r, V, D, workspace, dXB=None, XB=None, XA=None, Z=None, M=None, stream=None,
+                      info: bool = False):
+    """One analysis.  Returns an enkf_ism_info when ``info`` (the call then synchronises)."""
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    pdX, ldx = _mat(dXB, "dXB")
+    pXB, ldb = _mat(XB, "XB")
+    pXA, lda = _mat(XA, "XA")
+    pZ, ldz = _mat(Z, "Z")
+    inf = enkf_ism_info() if info else None
+    ws_bytes = workspace.numel() * workspace.element_size()
+    st = load().enkf_ism_analysis(plan, _ptr(r, "r"), pV, ldv, pD, ldd, pdX, ldx, pXB, ldb, pXA, lda, pZ, ldz,
+                                  _ptr(M, "M"), _ptr(workspace, "workspace"), ws_bytes, _stream(stream),
+                                  ctypes.byref(inf) if inf is not None else None)
+    _check(st)
+    return inf
+
+
+def enkf_ism_profile(plan, enable: bool) -> None:
+    _check(load().enkf_ism_profile(plan, 1 if enable else 0))
+
+
+def enkf_ism_profile_read(plan):
+    """{phase name: (total ms, launches)} of the phases recorded since the last read."""
+    ms = (ctypes.c_double * ENKF_PROFILE_PHASES)()
+    cnt = (ctypes.c_int32 * ENKF_PROFILE_PHASES)()
+    _check(load().enkf_ism_profile_read(plan, ms, cnt))
+    return {PROFILE_PHASE_NAMES[i]: (ms[i], cnt[i]) for i in range(ENKF_PROFILE_PHASES) if cnt[i]}
+
+
+def enkf_status_string(status: int) -> str:
+    return load().enkf_status_string(status).decode()
+
+
+def enkf_last_error() -> str:
+    return load().enkf_last_error().decode()
+
+
+class Plan:
+    """Owns a plan handle and its device workspace (allocated by torch)."""
+
+    def __init__(self, nstate, nobs, nens, mode, panel_b=0, flags=0, device=None):
+        import torch
+        self.handle, self.workspace_bytes = enkf_ism_plan(nstate, nobs, nens, mode, panel_b, flags)
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        # 256-byte alignment: torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=dev)
+        self.nstate, self.nobs, self.nens, self.mode = nstate, nobs, nens, mode
+
+    def close(self):
+        if self.handle is not None:
+            enkf_ism_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def analysis(self, r, V, D, **kw):
+        return enkf_ism_analysis(self.handle, r, V, D, self.workspace, **kw)
+
+    def obs_prep(self, obs_stride, center, XB, dXB, V, Y=None, D=None, stream=None):
+        enkf_obs_prep(self.handle, obs_stride, center, XB, dXB, V, Y, D, stream)

@@ -1,0 +1,282 @@
+"""Parity of the plain level-streaming path (FP64 and FP32) with the FP64 oracle.
+
+Every case runs through the C ABI (enkf_ism_plan / enkf_obs_prep /
+enkf_ism_analysis) on seeded synthetic inputs; the oracle receives exactly the
+values the device sees (FP32 inputs are rounded first).  Tolerances: relative
+Frobenius error <= 1e-10 for FP64 and <= 1e-5 for FP32 on Z and X_A.  M = V^T Z
+/ sqrt(Nens-1) is damped by 1/gamma in range(V) and so carries the conditioning
+of R + V V^T: its FP32 bar is 1e-5 * max(1, gamma_max / 100) (stated per case).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.util import host, rel, rounded, to_dev, vec_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1302_3876_gb300 import enkf  # noqa: E402
+
+TOL = {enkf.ENKF_FP64: 1e-10, enkf.ENKF_FP32: 1e-5}
+NP = {enkf.ENKF_FP64: np.float64, enkf.ENKF_FP32: np.float32}
+TT = {enkf.ENKF_FP64: torch.float64, enkf.ENKF_FP32: torch.float32}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    enkf.load(build_if_missing=True)
+
+
+def random_problem(seed, nobs, nens, nstate=None, spread=1.0):
+    nstate = nobs if nstate is None else nstate
+    s = synth.uniform(seed, 1, nstate, 0.5, 2.0) * spread
+    dXB = synth.normal_matrix(seed, 2, nstate, nens, row_scale=s)
+    V = synth.normal_matrix(seed, 5, nobs, nens, std=1.0 / math.sqrt(max(nens - 1, 1)),
+                            row_scale=synth.uniform(seed, 6, nobs, 0.5, 2.0))
+    r = synth.uniform(seed, 3, nobs, 0.5, 1.5)
+    D = synth.normal_matrix(seed, 4, nobs, nens)
+    XB = dXB + synth.normal_matrix(seed, 7, nstate, 1, mean=1.0)[0][None, :]
+    return r, V, D, dXB, XB
+
+
+def run_device(mode, r, V, D, dXB=None, XB=None, ld_pad=0, info=True, flags=0, alias=False):
+    dt = NP[mode]
+    nens, nobs = V.shape
+    nstate = dXB.shape[1] if dXB is not None else 1
+    plan = enkf.Plan(nstate, nobs, nens, mode, flags=flags)
+    tV = to_dev(V, dt, nobs + ld_pad)
+    tD = to_dev(D, dt, nobs + ld_pad)
+    tr = vec_dev(r, dt)
+    tZ = to_dev(np.zeros((nens, nobs)), dt, nobs + ld_pad)
+    tM = torch.zeros(nens * nens, dtype=TT[mode], device="cuda") if nens >= 2 else None
+    out = {}
+    kw = {}
+    if dXB is not None:
+        tdX = to_dev(dXB, dt, nstate + ld_pad)
+        tXB = to_dev(XB, dt, nstate + ld_pad)
+        tXA = tXB if alias else to_dev(np.zeros_like(XB), dt, nstate + ld_pad)
+        kw = dict(dXB=tdX, XB=tXB, XA=tXA)
+    inf = plan.analysis(tr, tV, tD, Z=tZ, M=tM, info=info, **kw)
+    torch.cuda.synchronize()
+    out["Z"] = host(tZ)
+    if tM is not None:
+        out["M"] = host(tM).reshape(nens, nens).T     # column-major nens x nens -> M[m, e]
+    if dXB is not None:
+        out["XA"] = host(kw["XA"])
+    out["info"] = inf
+    plan.close()
+    return out
+
+
+def oracle_of(mode, r, V, D, dXB=None, XB=None):
+    dt = NP[mode]
+    r64, V64, D64 = rounded(r, dt), rounded(V, dt), rounded(D, dt)
+    Z, gamma = oracle.ism_solve(r64, V64, D64, return_gamma=True)
+    out = {"Z": Z, "gamma": gamma}
+    if V.shape[0] >= 2:
+        out["M"] = oracle.vtz(V64, Z)
+    if dXB is not None:
+        dX64, XB64 = rounded(dXB, dt), rounded(XB, dt)
+        out["XA"] = oracle.analysis_update(XB64, dX64, out["M"])
+    return out
+
+
+def m_tol(mode, gamma_max):
+    return TOL[mode] * max(1.0, gamma_max / 100.0)
+
+
+CASES = [(1, 1), (2, 2), (3, 2), (31, 3), (33, 17), (127, 5), (129, 16), (1000, 32), (4099, 64), (20000, 48)]
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+@pytest.mark.parametrize("nobs,nens", CASES)
+def test_solve_and_analysis_random(mode, nobs, nens):
+    nstate = 3 * nobs + 5
+    r, V, D, dXB, XB = random_problem(7000 + nobs + 13 * nens, nobs, nens, nstate)
+    want_xa = nens >= 2
+    dev = run_device(mode, r, V, D, dXB if want_xa else None, XB if want_xa else None)
+    ref = oracle_of(mode, r, V, D, dXB if want_xa else None, XB if want_xa else None)
+    assert rel(dev["Z"], ref["Z"]) <= TOL[mode]
+    inf = dev["info"]
+    assert inf.status == 0
+    assert inf.gamma_min == pytest.approx(ref["gamma"].min(), rel=10 * TOL[mode])
+    assert inf.gamma_max == pytest.approx(ref["gamma"].max(), rel=10 * TOL[mode])
+    if want_xa:
+        assert rel(dev["M"], ref["M"]) <= m_tol(mode, ref["gamma"].max())
+        assert rel(dev["XA"], ref["XA"]) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+def test_padded_and_unaligned_leading_dimensions(mode):
+    """ld > rows (padded, vector path) and an odd ld (scalar path) give the same result."""
+    nobs, nens = 777, 9
+    r, V, D, dXB, XB = random_problem(11, nobs, nens, 2000)
+    ref = oracle_of(mode, r, V, D, dXB, XB)
+    for pad in (0, 32, 3):
+        dev = run_device(mode, r, V, D, dXB, XB, ld_pad=pad)
+        assert rel(dev["Z"], ref["Z"]) <= TOL[mode], pad
+        assert rel(dev["XA"], ref["XA"]) <= TOL[mode], pad
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+def test_xa_aliases_xb(mode):
+    nobs, nens = 500, 12
+    r, V, D, dXB, XB = random_problem(12, nobs, nens, 1500)
+    ref = oracle_of(mode, r, V, D, dXB, XB)
+    dev = run_device(mode, r, V, D, dXB, XB, alias=True)
+    assert rel(dev["XA"], ref["XA"]) <= TOL[mode]
+
+
+def test_zero_deviations():
+    """V = 0: gamma_k = 1 and Z = R^-1 D exactly; M = 0 and X_A = X_B."""
+    nobs, nens = 300, 8
+    r, V, D, dXB, XB = random_problem(13, nobs, nens, 600)
+    V[:] = 0.0
+    dev = run_device(enkf.ENKF_FP64, r, V, D, dXB, XB)
+    np.testing.assert_array_equal(dev["Z"], D / r[None, :])
+    assert dev["info"].gamma_min == 1.0 and dev["info"].gamma_max == 1.0
+    np.testing.assert_array_equal(dev["M"], 0.0)
+    np.testing.assert_array_equal(dev["XA"], XB)
+
+
+def test_deterministic_bitwise():
+    nobs, nens = 50000, 40
+    r, V, D, dXB, XB = random_problem(14, nobs, nens, 80000)
+    a = run_device(enkf.ENKF_FP32, r, V, D, dXB, XB)
+    b = run_device(enkf.ENKF_FP32, r, V, D, dXB, XB)
+    for k in ("Z", "M", "XA"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+def test_lorenz_small_full_pipeline(mode):
+    """Lorenz-96 Nstate=40, Nens=20, every 2nd variable observed, R = 0.01 I:
+    obs-space prep on the device (centering, H, 1/sqrt(Nens-1), D = Y - H X_B), then the analysis."""
+    d = synth.lorenz_small_draws()
+    dt = NP[mode]
+    truth = oracle.l96_rk4(d["truth0"], F=d["F"], dt=0.01, nsteps=1000)[0]
+    XB = rounded(truth[None, :] + d["ens_noise"], dt)
+    Y = rounded((truth[::2] + d["obs_noise"])[None, :] + d["pert"], dt)
+    r = np.full(d["nobs"], d["r"])
+    # oracle
+    _, dXB_o = oracle.ensemble_deviations(XB)
+    V_o = oracle.observe_deviations(dXB_o, d["nobs"], 2)
+    D_o = oracle.innovations(Y, XB, 2)
+    ref = oracle.analysis(r, V_o, D_o, XB, dXB_o)
+    # device
+    plan = enkf.Plan(d["nstate"], d["nobs"], d["nens"], mode)
+    tXB = to_dev(XB, dt)
+    tdX = to_dev(np.zeros_like(XB), dt)
+    tY = to_dev(Y, dt)
+    tV = to_dev(np.zeros((d["nens"], d["nobs"])), dt)
+    tD = to_dev(np.zeros((d["nens"], d["nobs"])), dt)
+    plan.obs_prep(2, 1, tXB, tdX, tV, Y=tY, D=tD)
+    tXA = to_dev(np.zeros_like(XB), dt)
+    tZ = to_dev(np.zeros((d["nens"], d["nobs"])), dt)
+    plan.analysis(vec_dev(r, dt), tV, tD, dXB=tdX, XB=tXB, XA=tXA, Z=tZ, info=True)
+    torch.cuda.synchronize()
+    tol = TOL[mode]
+    assert rel(host(tdX), dXB_o) <= tol
+    assert rel(host(tV), V_o) <= tol
+    assert rel(host(tD), D_o) <= tol
+    assert rel(host(tZ), ref["Z"]) <= tol
+    assert rel(host(tXA), ref["XA"]) <= tol
+    plan.close()
+
+
+# ---------------------------------------------------------------------------
+# Error paths: statuses, never a fault
+# ---------------------------------------------------------------------------
+
+def test_nonpositive_variance_is_a_numeric_error():
+    nobs, nens = 100, 4
+    r, V, D, _, _ = random_problem(15, nobs, nens)
+    r[37] = 0.0
+    with pytest.raises(enkf.EnkfError) as e:
+        run_device(enkf.ENKF_FP64, r, V, D)
+    assert e.value.status == enkf.ENKF_ERR_NUMERIC
+
+
+def test_nan_innovation_is_a_numeric_error():
+    nobs, nens = 100, 4
+    r, V, D, _, _ = random_problem(16, nobs, nens)
+    D[2, 5] = np.nan
+    with pytest.raises(enkf.EnkfError) as e:
+        run_device(enkf.ENKF_FP32, r, V, D)
+    assert e.value.status == enkf.ENKF_ERR_NUMERIC
+
+
+def test_bounded_barrier_wait_expires_with_a_status():
+    """One CTA never arrives (test flag); the others' bounded wait returns ENKF_ERR_TIMEOUT."""
+    nobs, nens = 200000, 8
+    r, V, D, _, _ = random_problem(17, nobs, nens)
+    with pytest.raises(enkf.EnkfError) as e:
+        run_device(enkf.ENKF_FP32, r, V, D, flags=enkf.ENKF_FLAG_TEST_TIMEOUT)
+    assert e.value.status == enkf.ENKF_ERR_TIMEOUT
+    # the context is still usable afterwards
+    dev = run_device(enkf.ENKF_FP32, r, V, D)
+    assert dev["info"].status == 0
+
+
+def test_argument_errors():
+    plan = enkf.Plan(100, 50, 4, enkf.ENKF_FP32)
+    r = torch.ones(50, device="cuda")
+    V = torch.zeros(4, 50, device="cuda")
+    D = torch.zeros(4, 50, device="cuda")
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(enkf.EnkfError) as e:
+        enkf.enkf_ism_analysis(plan.handle, r, V, D, small)
+    assert e.value.status == enkf.ENKF_ERR_WORKSPACE
+    with pytest.raises(enkf.EnkfError) as e:
+        enkf.enkf_ism_analysis(plan.handle, r, torch.zeros(4, 40, device="cuda"), D, plan.workspace)
+    assert e.value.status == enkf.ENKF_ERR_SHAPE
+    plan.close()
+    plan1 = enkf.Plan(100, 50, 1, enkf.ENKF_FP32)
+    with pytest.raises(enkf.EnkfError) as e:
+        plan1.analysis(r, V[:1], D[:1], M=torch.zeros(1, device="cuda"))
+    assert e.value.status == enkf.ENKF_ERR_SHAPE
+    plan1.close()
+
+
+# ---------------------------------------------------------------------------
+# Full size: the large single analysis (Nstate=2^21, Nobs=2^19, Nens=128)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_FP32, enkf.ENKF_FP64])
+def test_large_single_full_size(mode):
+    """The benchmark's workload, in the benchmark's launch configuration: V from
+    the deviations on the device (every 4th row, 1/sqrt(Nens-1)), then the
+    analysis; every output compared with the oracle run on the same values."""
+    dt = NP[mode]
+    w = synth.large_single(dtype=dt)
+    nstate, nobs, nens = w["nstate"], w["nobs"], w["nens"]
+    plan = enkf.Plan(nstate, nobs, nens, mode)
+    tdX = torch.from_numpy(w["dXB"]).cuda()
+    tD = torch.from_numpy(w["D"]).cuda()
+    tr = torch.from_numpy(w["r"]).cuda()
+    tV = torch.zeros(nens, nobs, dtype=TT[mode], device="cuda")
+    plan.obs_prep(4, 0, None, tdX, tV)
+    tXA = torch.empty_like(tdX)
+    tZ = torch.empty(nens, nobs, dtype=TT[mode], device="cuda")
+    tM = torch.empty(nens * nens, dtype=TT[mode], device="cuda")
+    inf = plan.analysis(tr, tV, tD, dXB=tdX, XB=tdX, XA=tXA, Z=tZ, M=tM, info=True)
+    assert inf.status == 0
+    dX64 = w["dXB"].astype(np.float64)
+    del w
+    V_o = oracle.observe_deviations(dX64, nobs, 4)
+    assert rel(host(tV), V_o) <= TOL[mode]
+    r64 = host(tr)
+    D64 = host(tD)
+    Z, gamma = oracle.ism_solve(r64, V_o, D64, return_gamma=True)
+    assert rel(host(tZ), Z) <= TOL[mode]
+    M = oracle.vtz(V_o, Z)
+    assert rel(host(tM).reshape(nens, nens).T, M) <= m_tol(mode, gamma.max())
+    XA = oracle.analysis_update(dX64, dX64, M)
+    assert rel(host(tXA), XA) <= TOL[mode]
+    plan.close()
