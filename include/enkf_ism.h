@@ -168,6 +168,29 @@ ENKF_API enkf_status enkf_ism_analysis(enkf_ism_plan_t plan,
                               void* stream, enkf_ism_info* info);
 
 /*
+ * enkf_forecast -- forecast step X_B(t_next) = M(X_A(t_cur)) (Sec. 2, eq. forecast-step)
+ * for the Lorenz-96 model of Sec. 4.2 (eq. eqn:Lorenz96, periodic, forcing F), in place.
+ *
+ *   X        nstate x nens ensemble (device, ld >= nstate), overwritten.
+ *   precision ENKF_FP64 or ENKF_FP32 (element type of X).
+ *   method   ENKF_FORECAST_RK4: nsteps classical Runge-Kutta steps of size dt, one CTA
+ *            per member with the state in shared memory (nstate <= 6144 in FP64,
+ *            12288 in FP32); every operation is an explicitly rounded IEEE operation
+ *            in a fixed order, so the result is reproducible bit for bit.
+ *            ENKF_FORECAST_SURROGATE: the learned surrogate (see enkf_surrogate_*),
+ *            weights = its packed parameter buffer, nsteps surrogate applications.
+ *   workspace / workspace_bytes: device scratch (size from enkf_forecast_workspace;
+ *            0 bytes for RK4, NULL allowed then).
+ * Returns ENKF_ERR_SHAPE for sizes out of range, ENKF_ERR_UNSUPPORTED otherwise.
+ */
+#define ENKF_FORECAST_RK4       0
+#define ENKF_FORECAST_SURROGATE 1
+ENKF_API enkf_status enkf_forecast(void* X, int64_t ld, int64_t nstate, int32_t nens, int32_t precision,
+                                   double F, double dt, int32_t nsteps, int32_t method, const void* weights,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+ENKF_API enkf_status enkf_forecast_workspace(int64_t nstate, int32_t nens, int32_t method, size_t* bytes);
+
+/*
  * Kernel-phase timing (tracing aid).  enkf_ism_profile(plan, 1) makes every later
  * enkf_obs_prep / enkf_ism_analysis call on the plan record CUDA events around
  * each of its kernel phases on the caller's stream (up to 4096 phases between

@@ -356,4 +356,35 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     return ENKF_OK;
 }
 
+enkf_status enkf_forecast_workspace(int64_t nstate, int32_t nens, int32_t method, size_t* bytes) {
+    if (!bytes) return fail(ENKF_ERR_ARG, "enkf_forecast_workspace: NULL bytes");
+    if (nstate < 1 || nens < 1) return fail(ENKF_ERR_SHAPE, "enkf_forecast_workspace: bad sizes");
+    if (method == ENKF_FORECAST_RK4) {
+        *bytes = 0;
+        return ENKF_OK;
+    }
+    return fail(ENKF_ERR_UNSUPPORTED, "enkf_forecast_workspace: method %d not built", method);
+}
+
+enkf_status enkf_forecast(void* X, int64_t ld, int64_t nstate, int32_t nens, int32_t precision, double F, double dt,
+                          int32_t nsteps, int32_t method, const void* weights, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+    (void)weights;
+    (void)workspace;
+    (void)workspace_bytes;
+    if (!X) return fail(ENKF_ERR_ARG, "enkf_forecast: NULL X");
+    if (precision != ENKF_FP64 && precision != ENKF_FP32) return fail(ENKF_ERR_ARG, "enkf_forecast: bad precision");
+    if (nstate < 4 || nens < 1 || ld < nstate || nsteps < 0)
+        return fail(ENKF_ERR_SHAPE, "enkf_forecast: need nstate >= 4, nens >= 1, ld >= nstate, nsteps >= 0");
+    const bool fp64 = precision == ENKF_FP64;
+    if ((uintptr_t)X % (fp64 ? 8 : 4)) return fail(ENKF_ERR_ARG, "enkf_forecast: X misaligned");
+    if (method == ENKF_FORECAST_RK4) {
+        if (nstate > (fp64 ? 6144 : 12288)) return fail(ENKF_ERR_SHAPE, "enkf_forecast: nstate too large for RK4");
+        if (nsteps == 0) return ENKF_OK;
+        CU(l96_rk4(fp64, X, ld, nstate, nens, F, dt, nsteps, (cudaStream_t)stream), "l96_rk4 launch");
+        return ENKF_OK;
+    }
+    return fail(ENKF_ERR_UNSUPPORTED, "enkf_forecast: method %d not built", method);
+}
+
 }  // extern "C"

@@ -35,6 +35,9 @@ ENKF_FLAG_REFINE = 0x1
 ENKF_FLAG_NO_CHECKS = 0x2
 ENKF_FLAG_TEST_TIMEOUT = 0x4
 
+ENKF_FORECAST_RK4 = 0
+ENKF_FORECAST_SURROGATE = 1
+
 ENKF_PROFILE_PHASES = 8
 PROFILE_PHASE_NAMES = ("obs_prep", "ism_levels", "gram_upper", "assemble_M", "xa_update", "", "", "")
 
@@ -84,6 +87,11 @@ def load(build_if_missing: bool = False):
         lib.enkf_ism_profile.restype = ctypes.c_int
         lib.enkf_ism_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         lib.enkf_ism_profile_read.restype = ctypes.c_int
+        dbl = ctypes.c_double
+        lib.enkf_forecast.argtypes = [vp, i64, i64, i32, i32, dbl, dbl, i32, i32, vp, vp, sz, vp]
+        lib.enkf_forecast.restype = ctypes.c_int
+        lib.enkf_forecast_workspace.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
+        lib.enkf_forecast_workspace.restype = ctypes.c_int
         lib.enkf_status_string.argtypes = [ctypes.c_int]
         lib.enkf_status_string.restype = ctypes.c_char_p
         lib.enkf_last_error.argtypes = []
@@ -173,6 +181,24 @@ def enkf_ism_analysis(plan, r, V, D, workspace, dXB=None, XB=None, XA=None, Z=No
                                   ctypes.byref(inf) if inf is not None else None)
     _check(st)
     return inf
+
+
+def enkf_forecast_workspace(nstate: int, nens: int, method: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().enkf_forecast_workspace(nstate, nens, method, ctypes.byref(b)))
+    return b.value
+
+
+def enkf_forecast(X, F: float, dt: float, nsteps: int, method: int = ENKF_FORECAST_RK4, weights=None,
+                  workspace=None, stream=None) -> None:
+    """Forecast in place; X is a CUDA tensor (nens, nstate) float64 or float32."""
+    import torch
+    pX, ld = _mat(X, "X")
+    nens, nstate = X.shape
+    precision = ENKF_FP64 if X.dtype == torch.float64 else ENKF_FP32
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check(load().enkf_forecast(pX, ld, nstate, nens, precision, F, dt, nsteps, method, _ptr(weights, "weights"),
+                                _ptr(workspace, "workspace"), ws_bytes, _stream(stream)))
 
 
 def enkf_ism_profile(plan, enable: bool) -> None:
