@@ -91,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -193,6 +193,11 @@ def run_reference(args):
 
 
 def run_ours(args):
+    global NSTATE, NOBS, WORKLOAD
+    if args.scale_div > 1:
+        NSTATE //= args.scale_div
+        NOBS //= args.scale_div
+        WORKLOAD = f"large_single/{args.scale_div} Nstate={NSTATE} Nobs={NOBS} Nens={NENS}"
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -267,15 +272,17 @@ def run_ours(args):
         step()
         h_XA.copy_(XA, non_blocking=True)
 
-    e2e_step()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
+    e2e_ms = float("nan")
+    if not args.no_e2e:
         e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
     h2d = h_dX.numel() * 4 + h_D.numel() * 4 + h_r.numel() * 4
     d2h = h_XA.numel() * 4
 
@@ -353,12 +360,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scale-div", type=int, default=1,
+                    help="divide Nobs and Nstate by this factor (small case for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
