@@ -204,6 +204,36 @@ ENKF_API enkf_status enkf_forecast_workspace(int64_t nstate, int32_t nens, int32
 ENKF_API enkf_status enkf_ism_profile(enkf_ism_plan_t plan, int32_t enable);
 ENKF_API enkf_status enkf_ism_profile_read(enkf_ism_plan_t plan, double* ms, int32_t* count);
 
+/*
+ * enkf_ism_solve_noalloc -- the solve Z = (R + V V^T)^{-1} D of enkf_ism_analysis
+ * (the same plain level-streaming kernel) without a caller-provided workspace.  The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * allocate device memory, such as a plugin whose host application already owns
+ * the GPU's memory through its own pool, or a process whose device-memory budget
+ * is fixed at start-up.
+ *
+ *   nobs, nens    sizes as for enkf_ism_plan (1 <= nens <= 1024).
+ *   precision     ENKF_FP64 or ENKF_FP32 (element type of r, V, D, Z).
+ *   r, V, D, Z    device pointers as for enkf_ism_analysis; Z (nobs x nens, ld ldz)
+ *                 is the output.
+ *   stream        cudaStream_t.
+ *   status        host int or NULL; when given, the call synchronises the stream and
+ *                 stores the device status word (0 = ok) there.
+ *
+ * Scratch lives in one static device array of ENKF_NOALLOC_SCRATCH_BYTES (32 MiB)
+ * that every GPU loading the library keeps until the process exits; the call
+ * allocates nothing.  Sizes whose scratch (U plus per-CTA partials, about
+ * w * nobs * nens bytes) exceeds the array are rejected with ENKF_ERR_WORKSPACE.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it: make that first
+ * call before any stream capture.  All calls share the array; calls that overlap
+ * on the GPU race on it.
+ */
+#define ENKF_NOALLOC_SCRATCH_BYTES (32u << 20)
+ENKF_API enkf_status enkf_ism_solve_noalloc(int64_t nobs, int32_t nens, int32_t precision, const void* r,
+                                            const void* V, int64_t ldv, const void* D, int64_t ldd,
+                                            void* Z, int64_t ldz, void* stream, int32_t* status);
+
 /* Human-readable name of a status code (static string). */
 ENKF_API const char* enkf_status_string(enkf_status s);
 

@@ -40,6 +40,8 @@ int64_t pad32(int64_t x) { return (x + 31) / 32 * 32; }
 
 }  // namespace
 
+void enkf::set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 struct enkf_ism_plan_s {
     int64_t nstate, nobs;
     int32_t nens, mode, panel_b;

@@ -65,6 +65,9 @@ cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int3
                      const void* XB, int64_t ldb, void* dXB, int64_t ldx, const void* Y, int64_t ldy,
                      void* V, int64_t ldv, void* D, int64_t ldd, cudaStream_t s);
 
+// Sets the text returned by enkf_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Lorenz-96 RK4 forecast, one CTA per member, state in shared memory.
 size_t rk4_smem(bool fp64, int64_t nstate);
 cudaError_t l96_rk4(bool fp64, void* X, int64_t ld, int64_t nstate, int32_t nens, double F, double dt, int32_t nsteps,

@@ -92,6 +92,9 @@ def load(build_if_missing: bool = False):
         lib.enkf_forecast.restype = ctypes.c_int
         lib.enkf_forecast_workspace.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
         lib.enkf_forecast_workspace.restype = ctypes.c_int
+        lib.enkf_ism_solve_noalloc.argtypes = [i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp,
+                                               ctypes.POINTER(i32)]
+        lib.enkf_ism_solve_noalloc.restype = ctypes.c_int
         lib.enkf_status_string.argtypes = [ctypes.c_int]
         lib.enkf_status_string.restype = ctypes.c_char_p
         lib.enkf_last_error.argtypes = []
@@ -199,6 +202,22 @@ def enkf_forecast(X, F: float, dt: float, nsteps: int, method: int = ENKF_FORECA
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(load().enkf_forecast(pX, ld, nstate, nens, precision, F, dt, nsteps, method, _ptr(weights, "weights"),
                                 _ptr(workspace, "workspace"), ws_bytes, _stream(stream)))
+
+
+def enkf_ism_solve_noalloc(r, V, D, Z, stream=None, sync: bool = True) -> int:
+    """Solve Z = (R + V V^T)^{-1} D without a workspace (scratch in the library's static
+    device array).  For callers that cannot allocate device memory.  Returns the
+    device status word when ``sync`` (the call then synchronises), else 0."""
+    import torch
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    pZ, ldz = _mat(Z, "Z")
+    nens, nobs = V.shape
+    precision = ENKF_FP64 if V.dtype == torch.float64 else ENKF_FP32
+    st = ctypes.c_int32(0)
+    _check(load().enkf_ism_solve_noalloc(nobs, nens, precision, _ptr(r, "r"), pV, ldv, pD, ldd, pZ, ldz,
+                                         _stream(stream), ctypes.byref(st) if sync else None))
+    return st.value
 
 
 def enkf_ism_profile(plan, enable: bool) -> None:
