@@ -1,0 +1,91 @@
+"""Pins of the FP64 surrogate oracle (oracle/surrogate.py) against independent facts:
+a circular convolution is a circulant matrix product; the network is equivariant to
+cyclic shifts of the state; gradients match central finite differences; Adam's first
+step has a closed form; GELU-tanh has known values and derivative."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import surrogate as S
+
+
+def params(seed=1):
+    return S.init_params(synth.normal_matrix(seed, 1, S.n_params(), 1)[0])
+
+
+def test_conv_is_a_circulant_product():
+    P = 7
+    W = synth.normal_matrix(2, 1, 5, 1)[0].reshape(1, 1, 5)
+    b = np.array([0.3])
+    z = synth.normal_matrix(2, 2, P, 1)[0].reshape(1, 1, P)
+    C = np.zeros((P, P))
+    for p in range(P):
+        for t in range(5):
+            C[p, (p + t - 2) % P] += W[0, 0, t]
+    np.testing.assert_allclose(S.conv(z, W, b)[0, 0], C @ z[0, 0] + 0.3, rtol=1e-14, atol=1e-14)
+
+
+def test_shift_equivariance():
+    pr = params()
+    x = 8.0 + synth.normal_matrix(3, 1, 40, 2)
+    y = S.forward(pr, x)
+    ys = S.forward(pr, np.roll(x, 5, axis=1))
+    np.testing.assert_allclose(ys, np.roll(y, 5, axis=1), rtol=1e-13, atol=1e-13)
+
+
+def test_gelu_values_and_derivative():
+    assert S.gelu(np.array(0.0)) == 0.0
+    assert S.gelu_grad(np.array(0.0)) == pytest.approx(0.5)
+    u = np.linspace(-4, 4, 17)
+    h = 1e-6
+    fd = (S.gelu(u + h) - S.gelu(u - h)) / (2 * h)
+    np.testing.assert_allclose(S.gelu_grad(u), fd, rtol=1e-7, atol=1e-9)
+    # large positive inputs pass through, large negative are cut
+    assert S.gelu(np.array(10.0)) == pytest.approx(10.0)
+    assert abs(S.gelu(np.array(-10.0))) < 1e-12
+
+
+def test_gradients_match_finite_differences():
+    pr = params(4)
+    # nonzero last-layer bias and weights so every path carries gradient
+    pr[3][1][:] = 0.05
+    x = 8.0 + 2.0 * synth.normal_matrix(4, 2, 11, 2)
+    tgt = x + 0.3 * synth.normal_matrix(4, 3, 11, 2)
+    _, grads = S.loss_and_grads(pr, x, tgt)
+    vec = S.flatten(pr)
+    gvec = S.flatten(grads)
+    rng_idx = (synth.u64(4, 5, 40) % np.uint64(vec.size)).astype(np.int64)
+    h = 1e-6
+    for i in rng_idx:
+        vp, vm = vec.copy(), vec.copy()
+        vp[i] += h
+        vm[i] -= h
+        lp = S.loss_and_grads(S.unflatten(vp), x, tgt)[0]
+        lm = S.loss_and_grads(S.unflatten(vm), x, tgt)[0]
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(gvec[i], rel=1e-5, abs=1e-9), i
+
+
+def test_adam_first_step_closed_form():
+    pr = params(5)
+    grads = [[np.full_like(W, 0.2), np.full_like(b, -3.0)] for W, b in pr]
+    before = S.flatten(pr)
+    st = {}
+    S.adam_step(pr, grads, st, lr=1e-3)
+    after = S.flatten(pr)
+    g = S.flatten(grads)
+    # after bias correction m_hat = g, v_hat = g^2: step = lr g / (|g| + eps)
+    np.testing.assert_allclose(after - before, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_rmse_time_mean():
+    truth = np.array([[1.0, 2.0], [0.0, 0.0]])
+    means = np.array([[1.0, 0.0], [3.0, 4.0]])
+    # per-time RMS: sqrt(4/2) and sqrt(25/2); time mean of those
+    assert S.rmse_time_mean(truth, means) == pytest.approx(0.5 * (math.sqrt(2.0) + math.sqrt(12.5)))
+
+
+def test_param_count():
+    assert S.n_params() == 64 * 5 + 64 + 2 * (64 * 64 * 5 + 64) + 64 * 5 + 1
