@@ -230,7 +230,8 @@ def run_ours(args):
     V = torch.empty(NENS, NOBS, dtype=torch.float32, device=dev)
     XA = torch.empty_like(dX)
     M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
-    plan = enkf.Plan(NSTATE, NOBS, NENS, enkf.ENKF_FP32, device=dev)
+    mode = enkf.ENKF_PANEL_FP32 if args.mode == "panel32" else enkf.ENKF_FP32
+    plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode == "panel32" else 0, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -324,7 +325,7 @@ def run_ours(args):
     if rank != 0:
         return
     peak, peak_kind = read_peaks()
-    lv_ms, lv_n = phases.get("ism_levels", (float("nan"), 0))
+    lv_ms, lv_n = phases.get("ism_solve", (float("nan"), 0))
     lv_avg = lv_ms / max(lv_n, 1)
     lb = level_bytes(NOBS, NENS, 4)
     achieved = lb / (lv_avg / 1e3) / 1e9
@@ -367,6 +368,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["panel32", "fp32"], default="panel32",
+                    help="headline path: panel form on FP32 CUDA cores, or the FP32 level-streaming path")
+    ap.add_argument("--panel-b", type=int, default=32)
     ap.add_argument("--scale-div", type=int, default=1,
                     help="divide Nobs and Nstate by this factor (small case for profiler captures)")
     args = ap.parse_args()

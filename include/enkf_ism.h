@@ -70,7 +70,8 @@ typedef enum {
     ENKF_FP64 = 0,        /* plain level-by-level path, double storage and arithmetic */
     ENKF_FP32 = 1,        /* plain level-by-level path, float storage, double gamma */
     ENKF_PANEL_BF16 = 2,  /* panel form, bf16 tensor-core trailing updates, FP64 denominators */
-    ENKF_PANEL_FP16 = 3   /* panel form, fp16 tensor-core trailing updates, FP64 denominators */
+    ENKF_PANEL_FP16 = 3,  /* panel form, fp16 tensor-core trailing updates, FP64 denominators */
+    ENKF_PANEL_FP32 = 4   /* panel form on FP32 CUDA cores (b levels per pass), FP64 denominators */
 } enkf_mode;
 
 /* Plan flags. */
@@ -101,7 +102,8 @@ typedef struct {
  *                    the solve only (M and X_A need nens >= 2, since S divides
  *                    by sqrt(Nens - 1)).
  *   mode             an enkf_mode.
- *   panel_b          panel width for the panel modes (0 = default); ignored otherwise.
+ *   panel_b          panel width for the panel modes (0 = default 32; ENKF_PANEL_FP32 takes
+ *                    1 <= panel_b <= 32); ignored otherwise.
  *   flags            ENKF_FLAG_* bits.
  *   workspace_bytes  receives the device workspace size enkf_ism_analysis needs.
  *
@@ -168,6 +170,62 @@ ENKF_API enkf_status enkf_ism_analysis(enkf_ism_plan_t plan,
                               void* stream, enkf_ism_info* info);
 
 /*
+ * Batched analyses: many independent problems of uneven size (for example the local
+ * analyses of a domain decomposition) solved in ONE persistent launch, replayed from
+ * a CUDA graph.  Each problem is the solve Z = (R + V V^T)^{-1} D of Sec. 3.1 plus
+ * M = V^T Z / sqrt(Nens - 1) (the ensemble-space factor of the SMEnKF update).
+ * FP32 storage with FP64 level denominators (ENKF_FP32 only).
+ *
+ * A problem is described by element offsets (in floats) into two caller buffers:
+ * base_in holds r (nobs), V and D (column-major, ld ldv / ldd); base_out receives
+ * Z (column-major, ld ldz; offset -1 to skip) and M (nens x nens column-major;
+ * offset -1 to skip).  2 <= nens <= 128 with nens % 4 == 0; nobs >= 1.
+ */
+typedef struct {
+    int64_t nobs;
+    int32_t nens;
+    int32_t reserved;         /* set to 0 */
+    int64_t r, V, D;          /* offsets into base_in */
+    int64_t ldv, ldd;
+    int64_t Z, ldz;           /* offset into base_out (or -1), leading dimension */
+    int64_t M;                /* offset into base_out (or -1) */
+} enkf_ism_problem;
+
+typedef struct enkf_ism_batch_plan_s* enkf_ism_batch_plan_t;
+
+/*
+ * enkf_ism_batch_plan -- host-side plan of a batch: validates the descriptors,
+ * orders the problems by cost (longest first), lays out the workspace and assigns
+ * each problem the panel width of its size class (nens x nobs bucket).  Widths come
+ * from the autotune cache file named by the environment variable
+ * ENKF_AUTOTUNE_CACHE when it holds this GPU's entries, else a default (16).
+ */
+ENKF_API enkf_status enkf_ism_batch_plan(enkf_ism_batch_plan_t* out, int32_t nprob, const enkf_ism_problem* problems,
+                                         int32_t mode, uint32_t flags, size_t* workspace_bytes);
+ENKF_API void enkf_ism_batch_plan_destroy(enkf_ism_batch_plan_t plan);
+
+/*
+ * enkf_ism_batch_autotune -- times every panel width b in {1, 8, 16, 32} on each size
+ * class of this batch (using the caller's data and workspace; synchronises the
+ * stream), keeps the fastest per class in the plan, and appends the choices to
+ * cache_path (or ENKF_AUTOTUNE_CACHE when cache_path is NULL; no file when both are
+ * absent).  widths (host, nullable) receives the 16 per-class choices.
+ */
+ENKF_API enkf_status enkf_ism_batch_autotune(enkf_ism_batch_plan_t plan, const void* base_in, void* base_out,
+                                             void* workspace, size_t workspace_bytes, void* stream,
+                                             const char* cache_path, int32_t* widths);
+
+/*
+ * enkf_ism_batch -- runs the batch.  The first call with a given (base_in, base_out,
+ * workspace) uploads the descriptor table into the workspace and captures a CUDA
+ * graph (on an internal stream); later calls with the same pointers replay it on
+ * `stream` (new data in place is fine).  status (host, nullable): when given, the
+ * call synchronises and stores the device status word.
+ */
+ENKF_API enkf_status enkf_ism_batch(enkf_ism_batch_plan_t plan, const void* base_in, void* base_out, void* workspace,
+                                    size_t workspace_bytes, void* stream, int32_t* status);
+
+/*
  * enkf_forecast -- forecast step X_B(t_next) = M(X_A(t_cur)) (Sec. 2, eq. forecast-step)
  * for the Lorenz-96 model of Sec. 4.2 (eq. eqn:Lorenz96, periodic, forcing F), in place.
  *
@@ -189,6 +247,33 @@ ENKF_API enkf_status enkf_forecast(void* X, int64_t ld, int64_t nstate, int32_t 
                                    double F, double dt, int32_t nsteps, int32_t method, const void* weights,
                                    void* workspace, size_t workspace_bytes, void* stream);
 ENKF_API enkf_status enkf_forecast_workspace(int64_t nstate, int32_t nens, int32_t method, size_t* bytes);
+
+/*
+ * Learned forecast surrogate (a stand-in for the model propagation of eq. forecast-step):
+ *   x_next = x + f(x), f = 4 periodic 1-D convolutions over the state index, channels
+ *   1 -> 64 -> 64 -> 64 -> 1, kernel 5, circular padding 2, GELU-tanh between layers,
+ *   input normalised as (x - 2.5) / 4.  BF16 weights and activations, FP32 accumulation.
+ * The FP32 master parameters are a flat vector in the order W1 (64,1,5), b1 (64),
+ * W2 (64,64,5), b2, W3 (64,64,5), b3, W4 (1,64,5), b4 (row-major (out, in, tap)).
+ * The packed buffer holds the BF16 / FP32 copies the kernels read (it is the `weights`
+ * argument of enkf_forecast with ENKF_FORECAST_SURROGATE).
+ *
+ * enkf_surrogate_sizes: parameter count, packed-buffer bytes, and the workspace bytes of
+ *   one training step on nbatch states of length nstate (any output pointer may be NULL).
+ * enkf_surrogate_pack: packed <- master (device pointers).
+ * enkf_surrogate_train_step: forward, MSE loss, backward on X -> target (nbatch x nstate,
+ *   contiguous FP32); writes the sum of squared errors to sq_err (device float) and the
+ *   flat gradient of the mean squared error to grad (device, nullable).  step >= 1 then
+ *   applies Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with t = step, learning
+ *   rate lr) to master / adam_m / adam_v and repacks; step = 0 computes gradients only.
+ */
+ENKF_API enkf_status enkf_surrogate_sizes(int64_t nstate, int32_t nbatch, int64_t* n_params, size_t* packed_bytes,
+                                          size_t* train_workspace_bytes);
+ENKF_API enkf_status enkf_surrogate_pack(const float* master, void* packed, void* stream);
+ENKF_API enkf_status enkf_surrogate_train_step(float* master, float* adam_m, float* adam_v, int32_t step, float lr,
+                                               void* packed, const float* X, const float* target, int64_t nstate,
+                                               int32_t nbatch, void* workspace, size_t workspace_bytes,
+                                               float* sq_err, float* grad, void* stream);
 
 /*
  * Kernel-phase timing (tracing aid).  enkf_ism_profile(plan, 1) makes every later

@@ -50,6 +50,7 @@ struct enkf_ism_plan_s {
     bool fp64;
     size_t w;                 // element size
     LevelLaunch L;
+    PanelLaunch P;
     int32_t nsplit;
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
@@ -110,11 +111,13 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     if (nens > 1024) return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: nens %d > 1024", nens);
     if (nobs > ((int64_t)1 << 40) || nstate > ((int64_t)1 << 40))
         return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: size too large");
-    if (mode != ENKF_FP64 && mode != ENKF_FP32) {
+    if (mode != ENKF_FP64 && mode != ENKF_FP32 && mode != ENKF_PANEL_FP32) {
         if (mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16)
-            return fail(ENKF_ERR_UNSUPPORTED, "enkf_ism_plan: panel modes are not built yet");
+            return fail(ENKF_ERR_UNSUPPORTED, "enkf_ism_plan: tensor-core panel modes are not built yet");
         return fail(ENKF_ERR_ARG, "enkf_ism_plan: bad mode %d", mode);
     }
+    if (mode == ENKF_PANEL_FP32 && (panel_b < 0 || panel_b > panel_max_b()))
+        return fail(ENKF_ERR_ARG, "enkf_ism_plan: panel_b %d out of [1, %d]", panel_b, panel_max_b());
     if (flags & ~(ENKF_FLAG_REFINE | ENKF_FLAG_NO_CHECKS | ENKF_FLAG_TEST_TIMEOUT))
         return fail(ENKF_ERR_ARG, "enkf_ism_plan: unknown flag bits 0x%x", flags);
     enkf_ism_plan_s* p = new (std::nothrow) enkf_ism_plan_s();
@@ -123,13 +126,19 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->nobs = nobs;
     p->nens = nens;
     p->mode = mode;
-    p->panel_b = 0;
+    p->panel_b = (mode == ENKF_PANEL_FP32) ? (panel_b > 0 ? panel_b : panel_max_b()) : 0;
     p->flags = flags;
     p->fp64 = (mode == ENKF_FP64);
     p->w = p->fp64 ? 8 : 4;
-    (void)panel_b;
     cudaError_t e = cudaGetDevice(&p->device);
-    if (e == cudaSuccess) e = level_plan(p->fp64, nobs, nens, &p->L);
+    if (e == cudaSuccess) {
+        if (mode == ENKF_PANEL_FP32) {
+            e = panel_plan(nobs, nens, p->panel_b, &p->P);
+            p->L.grid = p->P.grid;
+        } else {
+            e = level_plan(p->fp64, nobs, nens, &p->L);
+        }
+    }
     if (e != cudaSuccess) {
         delete p;
         return cuda_fail(e, "enkf_ism_plan: level_plan");
@@ -142,8 +151,10 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_ctl = o; o = align256(o + sizeof(Control));
     p->off_U = o; o = align256(o + p->w * (size_t)p->ldu * N);
     p->off_Z = o; o = align256(o + p->w * (size_t)p->ldzw * N);
-    p->off_part = o; o = align256(o + sizeof(double) * (size_t)p->L.grid * 2 * N);
-    p->off_coefg = o; o = align256(o + sizeof(double) * 2 * N);
+    const size_t part_per_cta = (mode == ENKF_PANEL_FP32) ? (size_t)p->P.part_stride : 2 * N;
+    const size_t coef_len = (mode == ENKF_PANEL_FP32) ? (size_t)p->P.part_stride : 2 * N;
+    p->off_part = o; o = align256(o + sizeof(double) * (size_t)p->L.grid * part_per_cta);
+    p->off_coefg = o; o = align256(o + sizeof(double) * coef_len);
     p->off_C = o; o = align256(o + sizeof(double) * N * N);
     p->off_gamma = o; o = align256(o + sizeof(double) * N);
     p->off_Qpart = o; o = align256(o + sizeof(double) * (size_t)p->nsplit * N * N);
@@ -301,7 +312,33 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     a.test_skip_arrival = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 1 : 0;
     a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
     int slot = prof_begin(p, 1, s);
-    CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
+    if (p->mode == ENKF_PANEL_FP32) {
+        PanelArgs pa;
+        pa.nobs = p->nobs;
+        pa.nens = p->nens;
+        pa.r = r;
+        pa.V = V;
+        pa.ldv = ldv;
+        pa.D = D;
+        pa.ldd = ldd;
+        pa.U = a.U;
+        pa.ldu = a.ldu;
+        pa.Z = a.Z;
+        pa.ldz = a.ldz;
+        pa.part = a.part;
+        pa.part_stride = p->P.part_stride;
+        pa.coefg = a.coefg;
+        pa.C = a.C;
+        pa.gamma = a.gamma;
+        pa.ctl = ctl;
+        pa.rows_per_blk = p->P.rows_per_blk;
+        pa.panel_b = p->panel_b;
+        pa.check = a.check;
+        pa.timeout_ns = a.timeout_ns;
+        CU(panel_launch(p->P, pa, s), "panel launch");
+    } else {
+        CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
+    }
     prof_end(p, slot, s);
 
     if (M || dXB) {
@@ -332,7 +369,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         memset(info, 0, sizeof(*info));
         info->status = st;
         info->grid_ctas = p->L.grid;
-        info->panel_b = 0;
+        info->panel_b = p->panel_b;
         double* g = (double*)malloc(sizeof(double) * (size_t)p->nens);
         if (!g) return fail(ENKF_ERR_ARG, "out of host memory");
         cudaError_t e = cudaMemcpy(g, a.gamma, sizeof(double) * (size_t)p->nens, cudaMemcpyDeviceToHost);
@@ -365,6 +402,10 @@ enkf_status enkf_forecast_workspace(int64_t nstate, int32_t nens, int32_t method
         *bytes = 0;
         return ENKF_OK;
     }
+    if (method == ENKF_FORECAST_SURROGATE) {
+        *bytes = surrogate_forecast_ws(nstate, nens);
+        return ENKF_OK;
+    }
     return fail(ENKF_ERR_UNSUPPORTED, "enkf_forecast_workspace: method %d not built", method);
 }
 
@@ -386,7 +427,53 @@ enkf_status enkf_forecast(void* X, int64_t ld, int64_t nstate, int32_t nens, int
         CU(l96_rk4(fp64, X, ld, nstate, nens, F, dt, nsteps, (cudaStream_t)stream), "l96_rk4 launch");
         return ENKF_OK;
     }
+    if (method == ENKF_FORECAST_SURROGATE) {
+        if (fp64) return fail(ENKF_ERR_UNSUPPORTED, "enkf_forecast: the surrogate runs on FP32 states");
+        if (!weights) return fail(ENKF_ERR_ARG, "enkf_forecast: NULL surrogate weights");
+        if (nstate < 5 || nstate > (1 << 28)) return fail(ENKF_ERR_SHAPE, "enkf_forecast: surrogate needs nstate >= 5");
+        const size_t need = surrogate_forecast_ws(nstate, nens);
+        if (!workspace || workspace_bytes < need || (uintptr_t)workspace % 256)
+            return fail(ENKF_ERR_WORKSPACE, "enkf_forecast: surrogate workspace %zu < %zu bytes (or misaligned)",
+                        workspace_bytes, need);
+        if ((uintptr_t)weights % 256) return fail(ENKF_ERR_ARG, "enkf_forecast: weights not 256-byte aligned");
+        CU(surrogate_forecast((float*)X, ld, nstate, nens, nsteps, weights, workspace, (cudaStream_t)stream),
+           "surrogate forecast");
+        return ENKF_OK;
+    }
     return fail(ENKF_ERR_UNSUPPORTED, "enkf_forecast: method %d not built", method);
+}
+
+enkf_status enkf_surrogate_sizes(int64_t nstate, int32_t nbatch, int64_t* n_params, size_t* packed_bytes,
+                                 size_t* train_workspace_bytes) {
+    if (nstate < 5 || nbatch < 1) return fail(ENKF_ERR_SHAPE, "enkf_surrogate_sizes: need nstate >= 5, nbatch >= 1");
+    if (n_params) *n_params = surrogate_n_params();
+    if (packed_bytes) *packed_bytes = surrogate_packed_bytes();
+    if (train_workspace_bytes) *train_workspace_bytes = surrogate_train_ws(nstate, nbatch);
+    return ENKF_OK;
+}
+
+enkf_status enkf_surrogate_pack(const float* master, void* packed, void* stream) {
+    if (!master || !packed) return fail(ENKF_ERR_ARG, "enkf_surrogate_pack: NULL argument");
+    if ((uintptr_t)packed % 256) return fail(ENKF_ERR_ARG, "enkf_surrogate_pack: packed not 256-byte aligned");
+    CU(surrogate_pack(master, packed, (cudaStream_t)stream), "surrogate pack");
+    return ENKF_OK;
+}
+
+enkf_status enkf_surrogate_train_step(float* master, float* adam_m, float* adam_v, int32_t step, float lr,
+                                      void* packed, const float* X, const float* target, int64_t nstate,
+                                      int32_t nbatch, void* workspace, size_t workspace_bytes, float* sq_err,
+                                      float* grad, void* stream) {
+    if (!master || !packed || !X || !target || !sq_err || (step > 0 && (!adam_m || !adam_v)))
+        return fail(ENKF_ERR_ARG, "enkf_surrogate_train_step: NULL argument");
+    if (nstate < 5 || nbatch < 1 || (int64_t)nstate * nbatch > ((int64_t)1 << 31))
+        return fail(ENKF_ERR_SHAPE, "enkf_surrogate_train_step: bad sizes");
+    const size_t need = surrogate_train_ws(nstate, nbatch);
+    if (!workspace || workspace_bytes < need || (uintptr_t)workspace % 256)
+        return fail(ENKF_ERR_WORKSPACE, "enkf_surrogate_train_step: workspace %zu < %zu bytes", workspace_bytes, need);
+    CU(surrogate_train_step(master, adam_m, adam_v, step, lr, packed, X, target, nstate, nbatch, workspace, sq_err,
+                            grad, (cudaStream_t)stream),
+       "surrogate train step");
+    return ENKF_OK;
 }
 
 }  // extern "C"

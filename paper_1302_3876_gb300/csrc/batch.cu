@@ -1,0 +1,404 @@
+// Batched iterative Sherman-Morrison analyses (many independent, uneven problems
+// in one persistent launch), FP32 storage with FP64 level denominators.
+//
+// One CTA solves one problem at a time; problems are taken from an atomic queue in
+// longest-processing-time order.  Inside a CTA the problem's iterates X = [U | Z]
+// live in a row-major copy (n x 2N) in the workspace, and the levels are applied
+// in panels of b levels (b = 1 is the plain level-by-level recurrence):
+//
+//   panel P = {k0, .., k0+b-1}, trailing columns x = u_i (i >= k0+b) and all z_i:
+//     a = V_P^T x                     (b dots per column, accumulated in the previous sweep)
+//     G = V_P^T U_P                   (the same dots for the panel's own columns)
+//     b x b recurrence in FP64 (eqs. SM-step-2-h/u restricted to the panel):
+//       gamma_m = 1 + (G beta_m)_m,   B[:,m] = beta_m / gamma_m,
+//       beta_j <- beta_j - B[:,m] (G beta_j)_m   (j > m),      so h_m = U_P B[:,m];
+//     c_m = v_m^T x^(m-1) = a_m - sum_{l<m} (G B)[m,l] c_l,  i.e. c = (I + L)^{-1} a;
+//     x <- x - sum_m h_m c_m = x - U_P (B (I + L)^{-1} a) = x - U_P W a,  W = B (I+L)^{-1}.
+//
+// Each sweep reads and writes every trailing column once, applies the whole
+// panel, and accumulates the next panel's a = V_{P'}^T x_new.  One thread owns one
+// trailing column (several row groups when there are fewer than 256 columns), so
+// the row-major layout makes every column access coalesced across a warp and the
+// panel rows of U_P and V_{P'} are warp broadcasts.  The panel width b is chosen
+// per size class by the autotuner (batch_tune in abi.cu).
+//
+// M = V^T Z / sqrt(N-1) is assembled without the cancellation of a direct product:
+// with chat_{k,i} = c_{k,i} / gamma_k (the per-level Z coefficients, from the panel
+// factor) and Q_km = v_k^T u_m^(m-1) (final, frozen U columns, materialised after
+// each panel), V^T Z = (I - triu(Q, 1)) chat -- the identity used by the single-
+// problem path.  Z is written back in the caller's column-major layout.
+#include <math.h>
+
+#include "internal.h"
+
+namespace enkf {
+namespace {
+
+constexpr int kBT = 256;      // threads per CTA
+constexpr int kBmax = 32;     // largest panel width
+
+struct SmemB {
+    float* apart;      // [kBT][kBmax]   per-thread partial dots
+    float* A;          // [kBmax][256]   reduced dots a_t of each active column
+    double* G;         // [kBmax][kBmax] panel Gram (FP64)
+    double* beta;      // [kBmax][kBmax]
+    double* Bm;        // [kBmax][kBmax]
+    double* L;         // [kBmax][kBmax]
+    float* W;          // [kBmax][kBmax] W = B (I + L)^{-1}
+    float* Bf;         // [kBmax][kBmax] gamma_m B[:,m] (final panel columns)
+    float* tile;       // [32][33] transpose tile
+    double* gam;       // [kBmax]
+    int* flag;         // [4]
+};
+
+__device__ __forceinline__ int col_of(int a, int N, int k1) {
+    // trailing columns after panel ending at k1: u_{k1..N-1}, then z_{0..N-1}
+    const int nu = N - k1;
+    return a < nu ? k1 + a : N + (a - nu);
+}
+
+// Step 1 into the row-major iterate: X[j][c] = V[j,c]/r_j, X[j][N+c] = D[j,c]/r_j, Vr[j][c] = V[j,c].
+// 32 x 32 tiles are read coalesced over rows and written coalesced over columns.
+__device__ void load_problem(const BatchDesc& d, const float* __restrict__ in, float* X, float* Vr, float* tile,
+                             Control* ctl) {
+    float* tile2 = tile + 32 * 33;
+    const int n = d.nobs, N = d.nens, ldX = d.ldX, ldVr = d.ldVr;
+    const float* r = in + d.r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncb = (2 * N + 31) / 32;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        for (int cb = 0; cb < ncb; ++cb) {
+            __syncthreads();
+            // read 32 rows x 32 columns (column-major source, coalesced over rows)
+            for (int cc = warp; cc < 32; cc += kBT / 32) {
+                const int c = cb * 32 + cc, j = j0 + lane;
+                float v = 0.f, src = 0.f;
+                if (c < 2 * N && j < n) {
+                    const float rj = r[j];
+                    src = c < N ? in[d.V + (int64_t)c * d.ldv + j] : in[d.D + (int64_t)(c - N) * d.ldd + j];
+                    if (!(rj > 0.f) || !isfinite(rj)) set_status(ctl, kErrNumeric);
+                    v = src / rj;
+                }
+                tile[cc * 33 + lane] = v;
+                tile2[cc * 33 + lane] = src;
+            }
+            __syncthreads();
+            for (int jj = warp; jj < 32; jj += kBT / 32) {
+                const int j = j0 + jj, c = cb * 32 + lane;
+                if (j < n && c < 2 * N) X[(int64_t)j * ldX + c] = tile[lane * 33 + jj];
+                if (j < n && c < N) Vr[(int64_t)j * ldVr + c] = tile2[lane * 33 + jj];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One sweep over the trailing columns of the panel ending at k1 (columns k1.. of U
+// and all of Z): if UPDATE, x -= U_P w with U_P = X[:, k0..k0+bp); if nb > 0,
+// accumulate a_t = V[:, k1+t]^T x_new for t < nb.  Leaves the reduced dots in s.A.
+template <int B>
+__device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB& s, int k0, int bp, int k1, int nb,
+                      bool update) {
+    const int n = d.nobs, N = d.nens, ldX = d.ldX, ldVr = d.ldVr;
+    const int ncols = (N - k1) + N;
+    const int G = kBT / ncols;           // row groups
+    const int t = threadIdx.x;
+    const bool active = t < G * ncols;
+    const int a = active ? t % ncols : 0;
+    const int g = active ? t / ncols : 0;
+    float w[B];
+    float acc[B], outer[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) acc[q] = 0.f, outer[q] = 0.f, w[q] = 0.f;
+    if (update && active) {
+        // w = W a_col for this column (a_col = dots of the panel's V with this column, index a + bp)
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            float sum = 0.f;
+            if (q < bp)
+                for (int u = 0; u < bp; ++u) sum = fmaf(s.W[q * kBmax + u], s.A[u * 256 + a + bp], sum);
+            w[q] = sum;
+        }
+    }
+    __syncthreads();   // s.A is rewritten below
+    if (active) {
+        const int col = col_of(a, N, k1);
+        int cnt = 0;
+        for (int j = g; j < n; j += G) {
+            float x = X[(int64_t)j * ldX + col];
+            if (update) {
+                const float* up = X + (int64_t)j * ldX + k0;
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (q < bp) x = fmaf(-up[q], w[q], x);
+                X[(int64_t)j * ldX + col] = x;
+            }
+            if (nb > 0) {
+                const float* vn = Vr + (int64_t)j * ldVr + k1;
+#pragma unroll
+                for (int q = 0; q < B; ++q)
+                    if (q < nb) acc[q] = fmaf(vn[q], x, acc[q]);
+                if (++cnt == 64) {
+                    cnt = 0;
+#pragma unroll
+                    for (int q = 0; q < B; ++q) outer[q] += acc[q], acc[q] = 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] = outer[q] + acc[q];
+    }
+    __syncthreads();
+    if (nb > 0) {
+        // reduce the row groups in a fixed order: A[q][a] = sum_g apart[(g*ncols + a)][q]
+        for (int e = threadIdx.x; e < nb * ncols; e += kBT) {
+            const int q = e / ncols, aa = e % ncols;
+            float sum = 0.f;
+            for (int gg = 0; gg < G; ++gg) sum += s.apart[(gg * ncols + aa) * kBmax + q];
+            s.A[q * 256 + aa] = sum;
+        }
+    }
+    __syncthreads();
+}
+
+// Panel factor from the Gram G = A[:, 0..bp) (FP64): gamma, B, L = (G B) strictly lower,
+// W = B (I + L)^{-1}.  Returns false (and latches kErrNumeric) on a bad gamma.
+__device__ bool factor(const SmemB& s, int bp, Control* ctl, bool check) {
+    const int t = threadIdx.x;
+    for (int e = t; e < bp * bp; e += kBT) {
+        const int q = e / bp, u = e % bp;
+        s.G[q * kBmax + u] = (double)s.A[q * 256 + u];      // G[t][s] = v_t^T u_s
+        s.beta[q * kBmax + u] = (q == u) ? 1.0 : 0.0;        // beta[row][col j]
+    }
+    __syncthreads();
+    if (t < 32) {
+        // lane j owns column beta_j; sequential over m
+        for (int m = 0; m < bp; ++m) {
+            // (G beta_j)_m for every j >= m (lane j)
+            double gm = 0.0;
+            if (t >= m && t < bp)
+                for (int u = 0; u < bp; ++u) gm += s.G[m * kBmax + u] * s.beta[u * kBmax + t];
+            const double gmm = __shfl_sync(0xffffffffu, gm, m);
+            const double gam = 1.0 + gmm;
+            if (t == 0) s.gam[m] = gam;
+            // B[:, m] = beta_m / gamma_m (lanes over rows u)
+            if (t < bp) s.Bm[t * kBmax + m] = s.beta[t * kBmax + m] / gam;
+            __syncwarp();
+            if (t > m && t < bp)
+                for (int u = 0; u < bp; ++u) s.beta[u * kBmax + t] -= s.Bm[u * kBmax + m] * gm;
+            __syncwarp();
+        }
+        // L[m][l] = (G B)[m][l], l < m; lane l
+        for (int m = 0; m < bp; ++m) {
+            double v = 0.0;
+            if (t < m)
+                for (int u = 0; u < bp; ++u) v += s.G[m * kBmax + u] * s.Bm[u * kBmax + t];
+            if (t < bp) s.L[m * kBmax + t] = (t < m) ? v : 0.0;
+        }
+        __syncwarp();
+        // W = B (I + L)^{-1}: row q of W solves W[q,:] (I + L) = B[q,:], back substitution over columns
+        if (t < bp) {
+            double wr[kBmax];
+            for (int l = bp - 1; l >= 0; --l) {
+                double v = s.Bm[t * kBmax + l];
+                for (int m = l + 1; m < bp; ++m) v -= s.L[m * kBmax + l] * wr[m];
+                wr[l] = v;
+                s.W[t * kBmax + l] = (float)v;
+            }
+        }
+        __syncwarp();
+        if (t < bp)
+            for (int m = 0; m < bp; ++m) s.Bf[t * kBmax + m] = (float)(s.Bm[t * kBmax + m] * s.gam[m]);
+        if (t == 0 && check) {
+            for (int m = 0; m < bp; ++m) {
+                const double g = s.gam[m];
+                if (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g))
+                    set_status(ctl, kErrNumeric);
+            }
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Per-level Z coefficients of the panel [k0, k0+bp): c = (I + L)^{-1} a_z for every z
+// column (a_z = previous sweep's dots, index (N - k0) + i), stored as chat = c / gamma.
+__device__ void panel_z_coefficients(const BatchDesc& d, const SmemB& s, float* Ch, int k0, int bp) {
+    const int N = d.nens;
+    for (int i = threadIdx.x; i < N; i += kBT) {
+        float c[kBmax];
+        for (int m = 0; m < bp; ++m) {
+            float v = s.A[m * 256 + (N - k0) + i];
+            for (int l = 0; l < m; ++l) v = fmaf(-(float)s.L[m * kBmax + l], c[l], v);
+            c[m] = v;
+            Ch[(int64_t)(k0 + m) * N + i] = (float)((double)v / s.gam[m]);
+        }
+    }
+    __syncthreads();
+}
+
+// Final values of the panel's own columns, u_m^(m-1) = gamma_m U_P B[:,m], in place.
+__device__ void panel_final_columns(const BatchDesc& d, float* X, const SmemB& s, int k0, int bp) {
+    for (int j = threadIdx.x; j < d.nobs; j += kBT) {
+        float* row = X + (int64_t)j * d.ldX + k0;
+        float u[kBmax];
+        for (int q = 0; q < bp; ++q) u[q] = row[q];
+        for (int m = 0; m < bp; ++m) {
+            float v = 0.f;
+            for (int q = 0; q <= m; ++q) v = fmaf(u[q], s.Bf[q * kBmax + m], v);
+            row[m] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// M = V^T Z / sqrt(N-1) and Z out (column-major).  256 threads, thread -> (k, i) blocks.
+__device__ void finish_problem(const BatchDesc& d, float* __restrict__ out, const float* X, const float* Vr,
+                               float* tile, const float* Ch, float* ws_q) {
+    const int n = d.nobs, N = d.nens, ldX = d.ldX, ldVr = d.ldVr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Z out: transpose X[:, N..2N) -> Z (column-major)
+    if (d.Z >= 0) {
+        const int ncb = (N + 31) / 32;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            for (int cb = 0; cb < ncb; ++cb) {
+                __syncthreads();
+                for (int jj = warp; jj < 32; jj += kBT / 32) {
+                    const int j = j0 + jj, c = cb * 32 + lane;
+                    tile[jj * 33 + lane] = (j < n && c < N) ? X[(int64_t)j * ldX + N + c] : 0.f;
+                }
+                __syncthreads();
+                for (int cc = warp; cc < 32; cc += kBT / 32) {
+                    const int c = cb * 32 + cc, j = j0 + lane;
+                    if (j < n && c < N) out[d.Z + (int64_t)c * d.ldz + j] = tile[lane * 33 + cc];
+                }
+            }
+        }
+    }
+    if (d.M >= 0 && N >= 2) {
+        // Q_km = v_k^T u_m (k < m) in 4 x 4 blocks (N % 4 == 0), FP32 products folded into FP64
+        // every 32 rows; then M = (I - triu(Q,1)) chat / sqrt(N-1).
+        float* Qw = ws_q;
+        const int nb4 = N / 4;
+        for (int blk = threadIdx.x; blk < nb4 * nb4; blk += kBT) {
+            const int kb = blk % nb4, mb = blk / nb4;
+            if (kb > mb) continue;
+            float acc[16];
+            double accd[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0.f, accd[q] = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const float4 v = *reinterpret_cast<const float4*>(Vr + (int64_t)j * ldVr + 4 * kb);
+                const float4 u = *reinterpret_cast<const float4*>(X + (int64_t)j * ldX + 4 * mb);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+                const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) acc[q * 4 + p] = fmaf(vv[q], uu[p], acc[q * 4 + p]);
+                if ((j & 31) == 31) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) accd[q] += (double)acc[q], acc[q] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    Qw[(int64_t)(4 * kb + q) * N + 4 * mb + p] = (float)(accd[q * 4 + p] + (double)acc[q * 4 + p]);
+        }
+        __syncthreads();
+        const float scale = (float)(1.0 / sqrt((double)(N - 1)));
+        for (int e = threadIdx.x; e < N * N; e += kBT) {
+            const int k = e % N, i = e / N;
+            float v = Ch[(int64_t)k * N + i];
+            for (int m = k + 1; m < N; ++m) v = fmaf(-Qw[(int64_t)k * N + m], Ch[(int64_t)m * N + i], v);
+            out[d.M + e] = v * scale;
+        }
+    }
+    __syncthreads();
+}
+
+template <int B>
+__device__ void solve_problem(const BatchDesc& d, const float* in, float* out, float* ws, const SmemB& s,
+                              Control* ctl, bool check) {
+    float* X = ws + d.X;
+    float* Vr = ws + d.Vr;
+    float* Ch = ws + d.Ch;
+    const int N = d.nens;
+    load_problem(d, in, X, Vr, s.tile, ctl);
+    // initial dots of panel 0 with every column
+    int bp = B < N ? B : N;
+    sweep<B>(d, X, Vr, s, 0, 0, 0, bp, false);
+    for (int k0 = 0; k0 < N; k0 += B) {
+        bp = (N - k0) < B ? (N - k0) : B;
+        factor(s, bp, ctl, check);
+        panel_z_coefficients(d, s, Ch, k0, bp);
+        const int k1 = k0 + bp;
+        const int nb = (N - k1) < B ? (N - k1) : B;
+        sweep<B>(d, X, Vr, s, k0, bp, k1, nb, true);
+        panel_final_columns(d, X, s, k0, bp);
+    }
+    finish_problem(d, out, X, Vr, s.tile, Ch, ws + d.Qw);
+}
+
+__global__ void __launch_bounds__(kBT) ism_batch_kernel(const BatchDesc* __restrict__ desc,
+                                                        const int* __restrict__ order, int nprob,
+                                                        const float* in, float* out, float* ws, Control* ctl,
+                                                        int check, int force_b) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemB s;
+    s.apart = reinterpret_cast<float*>(smem_raw);
+    s.A = s.apart + kBT * kBmax;
+    s.G = reinterpret_cast<double*>(s.A + kBmax * 256);
+    s.beta = s.G + kBmax * kBmax;
+    s.Bm = s.beta + kBmax * kBmax;
+    s.L = s.Bm + kBmax * kBmax;
+    s.gam = s.L + kBmax * kBmax;
+    s.W = reinterpret_cast<float*>(s.gam + kBmax);
+    s.Bf = s.W + kBmax * kBmax;
+    s.tile = s.Bf + kBmax * kBmax;
+    s.flag = reinterpret_cast<int*>(s.tile + 2 * 32 * 33);
+    for (;;) {
+        if (threadIdx.x == 0) s.flag[0] = atomicAdd(&ctl->barrier, 1u);
+        __syncthreads();
+        const int idx = s.flag[0];
+        __syncthreads();
+        if (idx >= nprob) break;
+        const BatchDesc d = desc[order[idx]];
+        const int b = force_b > 0 ? force_b : d.b;
+        switch (b) {
+            case 1: solve_problem<1>(d, in, out, ws, s, ctl, check); break;
+            case 8: solve_problem<8>(d, in, out, ws, s, ctl, check); break;
+            case 16: solve_problem<16>(d, in, out, ws, s, ctl, check); break;
+            default: solve_problem<32>(d, in, out, ws, s, ctl, check); break;
+        }
+    }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes() {
+    return sizeof(float) * (size_t)kBT * kBmax + sizeof(float) * kBmax * 256 + sizeof(double) * 4 * kBmax * kBmax +
+           sizeof(double) * kBmax + 2 * sizeof(float) * kBmax * kBmax + sizeof(float) * 2 * 32 * 33 + 16;
+}
+
+cudaError_t batch_configure(int* grid) {
+    const size_t smem = batch_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(ism_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ism_batch_kernel, kBT, smem)) != cudaSuccess) return e;
+    *grid = nsm * (occ > 0 ? occ : 1);
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch(int grid, const BatchDesc* desc, const int* order, int nprob, const float* in, float* out,
+                         float* ws, Control* ctl, int check, int force_b, cudaStream_t s) {
+    ism_batch_kernel<<<grid, kBT, batch_smem_bytes(), s>>>(desc, order, nprob, in, out, ws, ctl, check, force_b);
+    return cudaGetLastError();
+}
+
+}  // namespace enkf

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace enkf {
@@ -45,6 +47,40 @@ struct LevelLaunch {
 cudaError_t level_plan(bool fp64, int64_t nobs, int32_t nens, LevelLaunch* out);
 cudaError_t level_launch(bool fp64, const LevelLaunch& L, LevelArgs a, cudaStream_t s);
 
+// Panel form (FP32 CUDA cores) of the solve for one problem.
+struct PanelArgs {
+    int64_t nobs;
+    int32_t nens;
+    const void* r;
+    const void* V; int64_t ldv;
+    const void* D; int64_t ldd;
+    void* U; int64_t ldu;
+    void* Z; int64_t ldz;
+    double* part;                  // [grid][part_stride] per-CTA partial dots of the next panel
+    int64_t part_stride;
+    double* coefg;                 // [b * 2N] reduced dots of the current panel
+    double* C;                     // [nens][nens] per-level Z coefficients
+    double* gamma;                 // [nens]
+    Control* ctl;
+    int32_t rows_per_blk;
+    int32_t panel_b;
+    int32_t check;
+    uint64_t timeout_ns;
+};
+
+struct PanelLaunch {
+    int grid;
+    int threads;
+    size_t smem;
+    int rows_per_blk;
+    int b;
+    int64_t part_stride;
+};
+
+int panel_max_b();
+cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, PanelLaunch* out);
+cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
+
 // Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,
 // partials in double; then Q = sum of the partials in a fixed order.
 cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
@@ -64,6 +100,35 @@ cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, i
 cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int32_t stride, int32_t center,
                      const void* XB, int64_t ldb, void* dXB, int64_t ldx, const void* Y, int64_t ldy,
                      void* V, int64_t ldv, void* D, int64_t ldd, cudaStream_t s);
+
+// Batched analyses: one device descriptor per problem (element offsets).
+struct BatchDesc {
+    int32_t nobs, nens, b, ldX, ldVr, pad;
+    int64_t r, V, D, Z, M;     // offsets into the caller's input (r, V, D) and output (Z, M) base; -1 = none
+    int64_t ldv, ldd, ldz;
+    int64_t X, Vr;             // offsets of the row-major iterate [U | Z] and of V (row-major) in the workspace
+    int64_t Ch, Qw;            // offsets of chat (N x N) and of the Gram Q (N x N) in the workspace
+};
+size_t batch_smem_bytes();
+cudaError_t batch_configure(int* grid);
+cudaError_t batch_launch(int grid, const BatchDesc* desc, const int* order, int nprob, const float* in, float* out,
+                         float* ws, Control* ctl, int check, int force_b, cudaStream_t s);
+
+// Learned forecast surrogate: views of the packed parameter buffer.
+struct SurrogatePacked {
+    __nv_bfloat16 *W2, *W3, *WT2, *WT3;   // [o][t][i] and [i][t][o] (tap-flipped)
+    float *W1, *b1, *b2, *b3, *W4, *b4;
+};
+int64_t surrogate_n_params();
+size_t surrogate_packed_bytes();
+size_t surrogate_forecast_ws(int64_t nstate, int32_t nens);
+size_t surrogate_train_ws(int64_t nstate, int32_t nbatch);
+cudaError_t surrogate_pack(const float* flat, void* packed, cudaStream_t s);
+cudaError_t surrogate_forecast(float* X, int64_t ld, int64_t nstate, int32_t nens, int32_t nsteps, const void* packed,
+                               void* ws, cudaStream_t s);
+cudaError_t surrogate_train_step(float* master, float* mom, float* vel, int32_t step, float lr, void* packed,
+                                 const float* X, const float* target, int64_t nstate, int32_t nbatch, void* ws,
+                                 float* loss, float* grad_out, cudaStream_t s);
 
 // Sets the text returned by enkf_last_error() on the calling thread.
 void set_last_error(const char* msg);

@@ -1,0 +1,404 @@
+// Panel form of the iterative Sherman-Morrison solve for one large problem, on
+// FP32 CUDA cores: b levels of Step 2 (eqs. SM-step-2-h/Z/u) per pass over HBM.
+//
+// For a panel P = {k0..k0+b-1} and every trailing column x (u_i, i >= k0+b, and
+// all z_i), with a = V_P^T x (dots accumulated in the previous pass) and the panel
+// Gram G = V_P^T U_P:
+//   gamma_m = 1 + (G beta_m)_m,  B[:,m] = beta_m / gamma_m,
+//   beta_j <- beta_j - B[:,m] (G beta_j)_m   (j > m)          (so h_m = U_P B[:,m])
+//   c = (I + L)^{-1} a,  L = strictly lower part of G B        (c_m = v_m^T x^(m-1))
+//   x <- x - U_P W a,    W = B (I + L)^{-1}
+// which is the level-by-level recurrence regrouped (equal in exact arithmetic).
+// The panel's own columns end as u_m^(m-1) = gamma_m U_P B[:,m]; they are written
+// back so that the Gram V^T U of the M assembly sees the same final U as the
+// level-by-level path.  The per-level Z coefficients c_{k,i} (rows of C) and
+// gamma_k are produced by the factor, in FP64.
+//
+// Layout: one persistent cooperative launch; each CTA owns a fixed block of rows.
+// Per panel: every CTA factors the b x b Gram redundantly (FP64), then sweeps its
+// rows in 64 x 64 tiles of X (column-major, coalesced 64-row segments): the
+// update GEMM X -= U_P W' (K = b) and the next panel's dots A' += V_{P'}^T X_new
+// (K = rows), both register-tiled from shared memory.  A' partials are reduced
+// across CTAs in a fixed order between two bounded grid barriers.
+#include <math.h>
+
+#include "internal.h"
+
+namespace enkf {
+namespace {
+
+constexpr int kPT = 256;    // threads
+constexpr int kPB = 32;     // largest panel width
+constexpr int RT = 64;      // rows per tile
+constexpr int CT = 64;      // columns per tile
+constexpr int XLD = RT + 4; // padded tile stride (keeps 16-byte alignment)
+
+struct PanelSmem {
+    double* G;      // [kPB][kPB]
+    double* beta;   // [kPB][kPB]
+    double* Bm;     // [kPB][kPB]
+    double* L;      // [kPB][kPB]
+    double* gam;    // [kPB]
+    double* red;    // [32]
+    float* W;       // [kPB][kPB]
+    float* Bf;      // [kPB][kPB]  gamma_m B[:,m] (for the final panel columns)
+    float* Wt;      // [kPB][CT]   W' = W A[:, tile]
+    float* Xs;      // [CT][XLD]
+    float* UPs;     // [kPB][RT]
+    float* VNs;     // [kPB][RT]
+    int* flag;      // [4]
+};
+
+__device__ __forceinline__ float* col_ptr(const PanelArgs& a, int c) {
+    return c < a.nens ? static_cast<float*>(a.U) + (int64_t)c * a.ldu
+                      : static_cast<float*>(a.Z) + (int64_t)(c - a.nens) * a.ldz;
+}
+
+// trailing column a of the panel ending at k1 -> full column index (U: [0,N), Z: [N,2N))
+__device__ __forceinline__ int trail_col(int a, int N, int k1) {
+    const int nu = N - k1;
+    return a < nu ? k1 + a : N + (a - nu);
+}
+
+// b x b factor from G (FP64), by one warp; lanes own columns j (j, j + 32, ...).
+__device__ void factor_warp(const PanelSmem& s, int bp) {
+    const int lane = threadIdx.x & 31;
+    for (int m = 0; m < bp; ++m) {
+        double gm[kPB / 32 + 1];
+        int cnt = 0;
+        for (int j = lane; j < bp; j += 32, ++cnt) {
+            double v = 0.0;
+            if (j >= m)
+                for (int u = 0; u < bp; ++u) v += s.G[m * kPB + u] * s.beta[u * kPB + j];
+            gm[cnt] = v;
+        }
+        // (G beta_m)_m lives on lane m % 32, slot m / 32
+        double mine = gm[0];
+        for (int q = 1; q <= (bp - 1) / 32; ++q)
+            if ((m >> 5) == q) mine = gm[q];
+        const double gmm = __shfl_sync(0xffffffffu, mine, m & 31);
+        const double gam = 1.0 + gmm;
+        if (lane == 0) s.gam[m] = gam;
+        for (int u = lane; u < bp; u += 32) s.Bm[u * kPB + m] = s.beta[u * kPB + m] / gam;
+        __syncwarp();
+        cnt = 0;
+        for (int j = lane; j < bp; j += 32, ++cnt)
+            if (j > m)
+                for (int u = 0; u < bp; ++u) s.beta[u * kPB + j] -= s.Bm[u * kPB + m] * gm[cnt];
+        __syncwarp();
+    }
+    for (int m = 0; m < bp; ++m) {
+        for (int l = lane; l < bp; l += 32) {
+            double v = 0.0;
+            if (l < m)
+                for (int u = 0; u < bp; ++u) v += s.G[m * kPB + u] * s.Bm[u * kPB + l];
+            s.L[m * kPB + l] = (l < m) ? v : 0.0;
+        }
+    }
+    __syncwarp();
+    for (int q = lane; q < bp; q += 32) {
+        double wr[kPB];
+        for (int l = bp - 1; l >= 0; --l) {
+            double v = s.Bm[q * kPB + l];
+            for (int m = l + 1; m < bp; ++m) v -= s.L[m * kPB + l] * wr[m];
+            wr[l] = v;
+            s.W[q * kPB + l] = (float)v;
+        }
+        for (int m = 0; m < bp; ++m) s.Bf[q * kPB + m] = (float)(s.Bm[q * kPB + m] * s.gam[m]);
+    }
+    __syncwarp();
+}
+
+// Cross-CTA sum of the partial dots in a fixed order: each CTA owns a slice of the
+// entries; a team of threads per entry sums a fixed residue class of CTAs, then
+// the team's subtotals are added in team order.
+__device__ bool reduce_panel(const PanelArgs& a, const PanelSmem& s, int nvals, unsigned& epoch) {
+    const unsigned nblk = gridDim.x;
+    if (!grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, s.flag)) return false;
+    const int per = (nvals + nblk - 1) / nblk;
+    const int e0 = blockIdx.x * per;
+    double* sub = reinterpret_cast<double*>(s.Xs);          // scratch: [kPT] doubles
+    for (int eb = 0; eb < per; eb += kPT) {
+        const int ne = min(kPT, per - eb);
+        const int teams = kPT / ne;
+        const int t = threadIdx.x, e = t % ne, g = t / ne;
+        double v = 0.0;
+        if (g < teams && e0 + eb + e < nvals)
+            for (unsigned b = g; b < nblk; b += teams) v += __ldcg(&a.part[(int64_t)b * a.part_stride + e0 + eb + e]);
+        __syncthreads();
+        sub[t] = v;
+        __syncthreads();
+        if (t < ne && e0 + eb + t < nvals) {
+            double tot = 0.0;
+            for (int gg = 0; gg < teams; ++gg) tot += sub[gg * ne + t];
+            __stcg(&a.coefg[e0 + eb + t], tot);
+        }
+    }
+    return grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, s.flag);
+}
+
+// One sweep over this CTA's rows for the panel [k0, k0+bp) (bp = 0: no update) and
+// the next panel [k1, k1+nb) (nb = 0: no dots).  A (reduced dots of the previous
+// sweep) is read from coefg with row stride ncols_prev = ncols + bp.
+__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
+                      int nb) {
+    const int N = a.nens;
+    const int ncols = (N - k1) + N;
+    const int ncols_prev = ncols + bp;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const float* V = static_cast<const float*>(a.V);
+    for (int c0 = 0; c0 < ncols; c0 += CT) {
+        const int ncl = min(CT, ncols - c0);
+        __syncthreads();
+        if (bp > 0) {
+            // W'[t][c] = sum_s W[t][s] A[s][c0 + c + bp]
+            for (int e = tid; e < bp * CT; e += kPT) {
+                const int t = e / CT, c = e % CT;
+                float v = 0.f;
+                if (c < ncl)
+                    for (int u = 0; u < bp; ++u)
+                        v = fmaf(s.W[t * kPB + u], (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]), v);
+                s.Wt[t * CT + c] = v;
+            }
+        }
+        // GEMM2 accumulators: thread -> column c = tid % 64, rows of A' t = tg + 4 q
+        const int gc = tid & 63, tg = tid >> 6;
+        float acc[kPB / 4], outer[kPB / 4];
+#pragma unroll
+        for (int q = 0; q < kPB / 4; ++q) acc[q] = 0.f, outer[q] = 0.f;
+        for (int64_t rr = 0; rr < nrows; rr += RT) {
+            const int nr = (int)min((int64_t)RT, nrows - rr);
+            const int64_t row0 = r0 + rr;
+            __syncthreads();
+            // stage X tile (columns c0.., rows row0..), U_P and V_{P'} tiles
+            for (int e = tid; e < CT * RT; e += kPT) {
+                const int c = e / RT, j = e % RT;
+                float v = 0.f;
+                if (c < ncl && j < nr) v = col_ptr(a, trail_col(c0 + c, N, k1))[row0 + j];
+                s.Xs[c * XLD + j] = v;
+            }
+            for (int e = tid; e < bp * RT; e += kPT) {
+                const int t = e / RT, j = e % RT;
+                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
+            }
+            for (int e = tid; e < nb * RT; e += kPT) {
+                const int t = e / RT, j = e % RT;
+                s.VNs[t * RT + j] = j < nr ? V[(int64_t)(k1 + t) * a.ldv + row0 + j] : 0.f;
+            }
+            __syncthreads();
+            if (bp > 0) {
+                // GEMM1: thread (ty, tx) -> rows 4 ty.., columns 4 tx..
+                float x[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = *reinterpret_cast<const float4*>(&s.Xs[(tx * 4 + q) * XLD + ty * 4]);
+                    x[0][q] = v.x, x[1][q] = v.y, x[2][q] = v.z, x[3][q] = v.w;
+                }
+                for (int t = 0; t < bp; ++t) {
+                    const float4 u = *reinterpret_cast<const float4*>(&s.UPs[t * RT + ty * 4]);
+                    const float4 w = *reinterpret_cast<const float4*>(&s.Wt[t * CT + tx * 4]);
+                    const float uu[4] = {u.x, u.y, u.z, u.w}, ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) x[i][q] = fmaf(-uu[i], ww[q], x[i][q]);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4*>(&s.Xs[(tx * 4 + q) * XLD + ty * 4]) =
+                        make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
+                __syncthreads();
+                // write the updated tile back (coalesced 64-row segments)
+                for (int e = tid; e < CT * RT; e += kPT) {
+                    const int c = e / RT, j = e % RT;
+                    if (c < ncl && j < nr) col_ptr(a, trail_col(c0 + c, N, k1))[row0 + j] = s.Xs[c * XLD + j];
+                }
+            }
+            if (nb > 0) {
+                // GEMM2: A'[t][gc] += sum_j VN[t][j] X[gc][j]
+                for (int j = 0; j < RT; j += 4) {
+                    const float4 xv = *reinterpret_cast<const float4*>(&s.Xs[gc * XLD + j]);
+#pragma unroll
+                    for (int q = 0; q < kPB / 4; ++q) {
+                        const int t = tg + 4 * q;
+                        if (t < nb) {
+                            const float4 vv = *reinterpret_cast<const float4*>(&s.VNs[t * RT + j]);
+                            acc[q] = fmaf(vv.x, xv.x, fmaf(vv.y, xv.y, fmaf(vv.z, xv.z, fmaf(vv.w, xv.w, acc[q]))));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kPB / 4; ++q) outer[q] += acc[q], acc[q] = 0.f;
+            }
+        }
+        if (nb > 0 && gc < ncl) {
+#pragma unroll
+            for (int q = 0; q < kPB / 4; ++q) {
+                const int t = tg + 4 * q;
+                if (t < nb) __stcg(&a.part[(int64_t)blockIdx.x * a.part_stride + t * ncols + c0 + gc], (double)outer[q]);
+            }
+        }
+    }
+    // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
+    if (bp > 0) {
+        for (int64_t rr = 0; rr < nrows; rr += RT) {
+            const int nr = (int)min((int64_t)RT, nrows - rr);
+            const int64_t row0 = r0 + rr;
+            __syncthreads();
+            for (int e = tid; e < bp * RT; e += kPT) {
+                const int t = e / RT, j = e % RT;
+                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
+            }
+            __syncthreads();
+            for (int e = tid; e < bp * RT; e += kPT) {
+                const int m = e / RT, j = e % RT;
+                float v = 0.f;
+                for (int u = 0; u <= m; ++u) v = fmaf(s.UPs[u * RT + j], s.Bf[u * kPB + m], v);
+                if (j < nr) col_ptr(a, k0 + m)[row0 + j] = v;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PanelSmem s;
+    s.G = reinterpret_cast<double*>(smem_raw);
+    s.beta = s.G + kPB * kPB;
+    s.Bm = s.beta + kPB * kPB;
+    s.L = s.Bm + kPB * kPB;
+    s.gam = s.L + kPB * kPB;
+    s.red = s.gam + kPB;
+    s.W = reinterpret_cast<float*>(s.red + 32);
+    s.Bf = s.W + kPB * kPB;
+    s.Wt = s.Bf + kPB * kPB;
+    s.Xs = s.Wt + kPB * CT;
+    s.UPs = s.Xs + CT * XLD;
+    s.VNs = s.UPs + kPB * RT;
+    s.flag = reinterpret_cast<int*>(s.VNs + kPB * RT);
+
+    const int N = a.nens, b = a.panel_b;
+    const int tid = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_blk;
+    const int64_t r1 = min(r0 + (int64_t)a.rows_per_blk, a.nobs);
+    const int64_t nrows = r1 > r0 ? r1 - r0 : 0;
+    unsigned epoch = 0;
+    const float* V = static_cast<const float*>(a.V);
+    const float* D = static_cast<const float*>(a.D);
+    const float* r = static_cast<const float*>(a.r);
+
+    // ---- Step 1 (eq. SM-step-1) on this CTA's rows
+    for (int c = tid / 64; c < 2 * N; c += kPT / 64) {
+        const float* src = c < N ? V + (int64_t)c * a.ldv : D + (int64_t)(c - N) * a.ldd;
+        float* dst = col_ptr(a, c);
+        for (int64_t j = tid % 64; j < nrows; j += 64) {
+            const float rj = r[r0 + j];
+            if (a.check && !(rj > 0.f && isfinite(rj))) {
+                set_status(a.ctl, kErrNumeric);
+                a.ctl->fail_level = 0;
+            }
+            dst[r0 + j] = src[r0 + j] / rj;
+        }
+    }
+    __syncthreads();
+    // ---- dots of panel 0 with every column
+    int nb = b < N ? b : N;
+    sweep(a, s, r0, nrows, 0, 0, 0, nb);
+    if (!reduce_panel(a, s, nb * 2 * N, epoch)) return;
+
+    for (int k0 = 0; k0 < N; k0 += b) {
+        const int bp = (N - k0) < b ? (N - k0) : b;
+        const int k1 = k0 + bp;
+        const int ncols_prev = (N - k0) + N;
+        // factor of the panel (every CTA, FP64)
+        for (int e = tid; e < bp * bp; e += kPT) {
+            const int t = e / bp, u = e % bp;
+            s.G[t * kPB + u] = __ldcg(&a.coefg[t * ncols_prev + u]);
+            s.beta[t * kPB + u] = (t == u) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (tid < 32) factor_warp(s, bp);
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            // gamma and the per-level Z coefficients c = (I + L)^{-1} a for every z column
+            if (tid < bp) a.gamma[k0 + tid] = s.gam[tid];
+            for (int i = tid; i < N; i += kPT) {
+                const int ai = (N - k0) + i;   // index of z_i among the previous sweep's columns
+                double c[kPB];
+                for (int m = 0; m < bp; ++m) {
+                    double v = __ldcg(&a.coefg[m * ncols_prev + ai]);
+                    for (int l = 0; l < m; ++l) v -= s.L[m * kPB + l] * c[l];
+                    c[m] = v;
+                    a.C[(int64_t)(k0 + m) * N + i] = v;
+                }
+            }
+            if (a.check && tid == 0) {
+                for (int m = 0; m < bp; ++m) {
+                    const double g = s.gam[m];
+                    if (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g)) {
+                        set_status(a.ctl, kErrNumeric);
+                        a.ctl->fail_level = k0 + m + 1;
+                    }
+                }
+            }
+        }
+        nb = (N - k1) < b ? (N - k1) : b;
+        // every CTA has read coefg; it is rewritten only after the next barrier
+        sweep(a, s, r0, nrows, k0, bp, k1, nb);
+        if (nb > 0) {
+            if (!reduce_panel(a, s, nb * ((N - k1) + N), epoch)) return;
+        } else {
+            break;
+        }
+    }
+}
+
+size_t panel_smem() {
+    return sizeof(double) * (4 * kPB * kPB + kPB + 32) + sizeof(float) * (2 * kPB * kPB + kPB * CT + CT * XLD +
+                                                                          2 * kPB * RT) + 16;
+}
+
+}  // namespace
+
+int panel_max_b() { return kPB; }
+
+cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, PanelLaunch* L) {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const size_t smem = panel_smem();
+    if ((e = cudaFuncSetAttribute(ism_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ism_panel_kernel, kPT, smem)) != cudaSuccess)
+        return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    occ = occ > 2 ? 2 : occ;
+    int64_t grid = (int64_t)nsm * occ;
+    const int64_t by_rows = (nobs + RT - 1) / RT;
+    if (grid > by_rows) grid = by_rows;
+    int64_t rpb = (nobs + grid - 1) / grid;
+    rpb = (rpb + 3) / 4 * 4;
+    grid = (nobs + rpb - 1) / rpb;
+    L->grid = (int)grid;
+    L->threads = kPT;
+    L->smem = smem;
+    L->rows_per_blk = (int)rpb;
+    L->b = b;
+    L->part_stride = (int64_t)b * 2 * nens;   // largest nb * ncols
+    return cudaSuccess;
+}
+
+cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s) {
+    a.rows_per_blk = L.rows_per_blk;
+    a.panel_b = L.b;
+    a.part_stride = L.part_stride;
+    void* args[] = {&a};
+    cudaError_t e = cudaFuncSetAttribute(ism_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void*)ism_panel_kernel, dim3(L.grid), dim3(L.threads), args, L.smem, s);
+}
+
+}  // namespace enkf

@@ -30,6 +30,7 @@ ENKF_FP64 = 0
 ENKF_FP32 = 1
 ENKF_PANEL_BF16 = 2
 ENKF_PANEL_FP16 = 3
+ENKF_PANEL_FP32 = 4
 
 ENKF_FLAG_REFINE = 0x1
 ENKF_FLAG_NO_CHECKS = 0x2
@@ -39,13 +40,20 @@ ENKF_FORECAST_RK4 = 0
 ENKF_FORECAST_SURROGATE = 1
 
 ENKF_PROFILE_PHASES = 8
-PROFILE_PHASE_NAMES = ("obs_prep", "ism_levels", "gram_upper", "assemble_M", "xa_update", "", "", "")
+PROFILE_PHASE_NAMES = ("obs_prep", "ism_solve", "gram_upper", "assemble_M", "xa_update", "", "", "")
 
 
 class EnkfError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{status_name(status)}: {message}")
         self.status = status
+
+
+class enkf_ism_problem(ctypes.Structure):
+    _fields_ = [("nobs", ctypes.c_int64), ("nens", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("r", ctypes.c_int64), ("V", ctypes.c_int64), ("D", ctypes.c_int64),
+                ("ldv", ctypes.c_int64), ("ldd", ctypes.c_int64), ("Z", ctypes.c_int64), ("ldz", ctypes.c_int64),
+                ("M", ctypes.c_int64)]
 
 
 class enkf_ism_info(ctypes.Structure):
@@ -95,6 +103,22 @@ def load(build_if_missing: bool = False):
         lib.enkf_ism_solve_noalloc.argtypes = [i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp,
                                                ctypes.POINTER(i32)]
         lib.enkf_ism_solve_noalloc.restype = ctypes.c_int
+        lib.enkf_ism_batch_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(enkf_ism_problem), i32, u32,
+                                            ctypes.POINTER(sz)]
+        lib.enkf_ism_batch_plan.restype = ctypes.c_int
+        lib.enkf_ism_batch_plan_destroy.argtypes = [vp]
+        lib.enkf_ism_batch_plan_destroy.restype = None
+        lib.enkf_ism_batch_autotune.argtypes = [vp, vp, vp, vp, sz, vp, ctypes.c_char_p, ctypes.POINTER(i32)]
+        lib.enkf_ism_batch_autotune.restype = ctypes.c_int
+        lib.enkf_ism_batch.argtypes = [vp, vp, vp, vp, sz, vp, ctypes.POINTER(i32)]
+        lib.enkf_ism_batch.restype = ctypes.c_int
+        lib.enkf_surrogate_sizes.argtypes = [i64, i32, ctypes.POINTER(i64), ctypes.POINTER(sz), ctypes.POINTER(sz)]
+        lib.enkf_surrogate_sizes.restype = ctypes.c_int
+        lib.enkf_surrogate_pack.argtypes = [vp, vp, vp]
+        lib.enkf_surrogate_pack.restype = ctypes.c_int
+        lib.enkf_surrogate_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, i64, i32, vp, sz, vp,
+                                                  vp, vp]
+        lib.enkf_surrogate_train_step.restype = ctypes.c_int
         lib.enkf_status_string.argtypes = [ctypes.c_int]
         lib.enkf_status_string.restype = ctypes.c_char_p
         lib.enkf_last_error.argtypes = []
@@ -218,6 +242,65 @@ def enkf_ism_solve_noalloc(r, V, D, Z, stream=None, sync: bool = True) -> int:
     _check(load().enkf_ism_solve_noalloc(nobs, nens, precision, _ptr(r, "r"), pV, ldv, pD, ldd, pZ, ldz,
                                          _stream(stream), ctypes.byref(st) if sync else None))
     return st.value
+
+
+def enkf_ism_batch_plan(problems, mode: int = ENKF_FP32, flags: int = 0):
+    """problems: sequence of dicts with keys nobs, nens, r, V, D, ldv, ldd, Z, ldz, M (float offsets).
+    Returns (batch plan handle, workspace bytes)."""
+    arr = (enkf_ism_problem * max(len(problems), 1))()
+    for i, p in enumerate(problems):
+        arr[i] = enkf_ism_problem(nobs=p["nobs"], nens=p["nens"], reserved=0, r=p["r"], V=p["V"], D=p["D"],
+                                  ldv=p["ldv"], ldd=p["ldd"], Z=p.get("Z", -1), ldz=p.get("ldz", p["nobs"]),
+                                  M=p.get("M", -1))
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check(load().enkf_ism_batch_plan(ctypes.byref(h), len(problems), arr, mode, flags, ctypes.byref(ws)))
+    return h, ws.value
+
+
+def enkf_ism_batch_plan_destroy(plan) -> None:
+    load().enkf_ism_batch_plan_destroy(plan)
+
+
+def enkf_ism_batch_autotune(plan, base_in, base_out, workspace, stream=None, cache_path=None):
+    """Returns the 16 per-class panel widths chosen."""
+    w = (ctypes.c_int32 * 16)()
+    _check(load().enkf_ism_batch_autotune(plan, _ptr(base_in, "base_in"), _ptr(base_out, "base_out"),
+                                          _ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                                          _stream(stream), cache_path.encode() if cache_path else None, w))
+    return list(w)
+
+
+def enkf_ism_batch(plan, base_in, base_out, workspace, stream=None, sync: bool = False) -> int:
+    st = ctypes.c_int32(0)
+    _check(load().enkf_ism_batch(plan, _ptr(base_in, "base_in"), _ptr(base_out, "base_out"),
+                                 _ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                                 _stream(stream), ctypes.byref(st) if sync else None))
+    return st.value
+
+
+def enkf_surrogate_sizes(nstate: int, nbatch: int):
+    """(number of parameters, packed bytes, training workspace bytes)."""
+    n = ctypes.c_int64()
+    pb = ctypes.c_size_t()
+    tw = ctypes.c_size_t()
+    _check(load().enkf_surrogate_sizes(nstate, nbatch, ctypes.byref(n), ctypes.byref(pb), ctypes.byref(tw)))
+    return n.value, pb.value, tw.value
+
+
+def enkf_surrogate_pack(master, packed, stream=None) -> None:
+    _check(load().enkf_surrogate_pack(_ptr(master, "master"), _ptr(packed, "packed"), _stream(stream)))
+
+
+def enkf_surrogate_train_step(master, adam_m, adam_v, step, lr, packed, X, target, workspace, sq_err, grad=None,
+                              stream=None) -> None:
+    """X, target: CUDA float32 (nbatch, nstate) contiguous."""
+    nbatch, nstate = X.shape
+    _check(load().enkf_surrogate_train_step(_ptr(master, "master"), _ptr(adam_m, "adam_m"), _ptr(adam_v, "adam_v"),
+                                            step, lr, _ptr(packed, "packed"), _ptr(X, "X"), _ptr(target, "target"),
+                                            nstate, nbatch, _ptr(workspace, "workspace"),
+                                            workspace.numel() * workspace.element_size(), _ptr(sq_err, "sq_err"),
+                                            _ptr(grad, "grad"), _stream(stream)))
 
 
 def enkf_ism_profile(plan, enable: bool) -> None:

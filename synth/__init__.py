@@ -202,3 +202,45 @@ def batch_local_problem(i: int, nobs: int, nens: int, seed: int | None = None, d
     r = uniform(seed, base + 2, nobs, 0.5, 1.5).astype(dtype)
     D = normal_matrix(seed, base + 3, nobs, nens, dtype=dtype)
     return {"V": V, "D": D, "r": r}
+
+
+def batch_local_packed(nprob: int = 8192, seed: int | None = None, nens_override=None, nobs_override=None):
+    """Packs the inputs of the batched workload into one float32 buffer.
+
+    Returns (base_in numpy float32, descriptors, out_floats, sizes): descriptor i
+    holds float offsets of r_i, V_i (column-major, ld = nobs_i), D_i and of the
+    outputs Z_i (column-major) and M_i (nens_i x nens_i) in an output buffer of
+    out_floats floats.  Offsets are multiples of 4 floats."""
+    seed = seed_for("batch_local") if seed is None else seed
+    nobs, nens = batch_local_sizes(nprob, seed)
+    if nens_override is not None:
+        nens = np.asarray(nens_override, dtype=np.int64)
+    if nobs_override is not None:
+        nobs = np.asarray(nobs_override, dtype=np.int64)
+
+    def up4(x):
+        return (int(x) + 3) // 4 * 4
+
+    descs, off_in, off_out = [], 0, 0
+    for i in range(nprob):
+        n, N = int(nobs[i]), int(nens[i])
+        d = {"nobs": n, "nens": N, "ldv": n, "ldd": n, "ldz": n}
+        d["r"] = off_in
+        off_in += up4(n)
+        d["V"] = off_in
+        off_in += up4(n * N)
+        d["D"] = off_in
+        off_in += up4(n * N)
+        d["Z"] = off_out
+        off_out += up4(n * N)
+        d["M"] = off_out
+        off_out += up4(N * N)
+        descs.append(d)
+    base = np.zeros(off_in, dtype=np.float32)
+    for i, d in enumerate(descs):
+        n, N = d["nobs"], d["nens"]
+        p = batch_local_problem(i, n, N, seed, dtype=np.float32)
+        base[d["r"]:d["r"] + n] = p["r"]
+        base[d["V"]:d["V"] + n * N] = p["V"].reshape(-1)
+        base[d["D"]:d["D"] + n * N] = p["D"].reshape(-1)
+    return base, descs, off_out

@@ -21,9 +21,10 @@ pytestmark = pytest.mark.gpu
 
 from paper_1302_3876_gb300 import enkf  # noqa: E402
 
-TOL = {enkf.ENKF_FP64: 1e-10, enkf.ENKF_FP32: 1e-5}
-NP = {enkf.ENKF_FP64: np.float64, enkf.ENKF_FP32: np.float32}
-TT = {enkf.ENKF_FP64: torch.float64, enkf.ENKF_FP32: torch.float32}
+TOL = {enkf.ENKF_FP64: 1e-10, enkf.ENKF_FP32: 1e-5, enkf.ENKF_PANEL_FP32: 1e-5}
+NP = {enkf.ENKF_FP64: np.float64, enkf.ENKF_FP32: np.float32, enkf.ENKF_PANEL_FP32: np.float32}
+TT = {enkf.ENKF_FP64: torch.float64, enkf.ENKF_FP32: torch.float32, enkf.ENKF_PANEL_FP32: torch.float32}
+MODES = [enkf.ENKF_FP64, enkf.ENKF_FP32, enkf.ENKF_PANEL_FP32]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,11 +46,11 @@ def random_problem(seed, nobs, nens, nstate=None, spread=1.0):
     return r, V, D, dXB, XB
 
 
-def run_device(mode, r, V, D, dXB=None, XB=None, ld_pad=0, info=True, flags=0, alias=False):
+def run_device(mode, r, V, D, dXB=None, XB=None, ld_pad=0, info=True, flags=0, alias=False, panel_b=0):
     dt = NP[mode]
     nens, nobs = V.shape
     nstate = dXB.shape[1] if dXB is not None else 1
-    plan = enkf.Plan(nstate, nobs, nens, mode, flags=flags)
+    plan = enkf.Plan(nstate, nobs, nens, mode, flags=flags, panel_b=panel_b)
     tV = to_dev(V, dt, nobs + ld_pad)
     tD = to_dev(D, dt, nobs + ld_pad)
     tr = vec_dev(r, dt)
@@ -94,7 +95,7 @@ def m_tol(mode, gamma_max):
 CASES = [(1, 1), (2, 2), (3, 2), (31, 3), (33, 17), (127, 5), (129, 16), (1000, 32), (4099, 64), (20000, 48)]
 
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("nobs,nens", CASES)
 def test_solve_and_analysis_random(mode, nobs, nens):
     nstate = 3 * nobs + 5
@@ -112,7 +113,7 @@ def test_solve_and_analysis_random(mode, nobs, nens):
         assert rel(dev["XA"], ref["XA"]) <= TOL[mode]
 
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_FP64, enkf.ENKF_FP32])
+@pytest.mark.parametrize("mode", MODES)
 def test_padded_and_unaligned_leading_dimensions(mode):
     """ld > rows (padded, vector path) and an odd ld (scalar path) give the same result."""
     nobs, nens = 777, 9
@@ -131,6 +132,21 @@ def test_xa_aliases_xb(mode):
     ref = oracle_of(mode, r, V, D, dXB, XB)
     dev = run_device(mode, r, V, D, dXB, XB, alias=True)
     assert rel(dev["XA"], ref["XA"]) <= TOL[mode]
+
+
+@pytest.mark.parametrize("panel_b", [1, 5, 8, 16, 32])
+def test_panel_widths(panel_b):
+    """The panel form regroups the levels; every width (ragged last panel included)
+    reaches the same result as the level-by-level oracle."""
+    nobs, nens = 9000, 45
+    r, V, D, dXB, XB = random_problem(31 + panel_b, nobs, nens, 20000)
+    ref = oracle_of(enkf.ENKF_PANEL_FP32, r, V, D, dXB, XB)
+    dev = run_device(enkf.ENKF_PANEL_FP32, r, V, D, dXB, XB, panel_b=panel_b)
+    assert dev["info"].panel_b == panel_b
+    assert rel(dev["Z"], ref["Z"]) <= 1e-5
+    assert dev["info"].gamma_max == pytest.approx(ref["gamma"].max(), rel=1e-4)
+    assert rel(dev["M"], ref["M"]) <= m_tol(enkf.ENKF_PANEL_FP32, ref["gamma"].max())
+    assert rel(dev["XA"], ref["XA"]) <= 1e-5
 
 
 def test_zero_deviations():
@@ -248,7 +264,7 @@ def test_argument_errors():
 # Full size: the large single analysis (Nstate=2^21, Nobs=2^19, Nens=128)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_FP32, enkf.ENKF_FP64])
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_FP32, enkf.ENKF_FP32, enkf.ENKF_FP64])
 def test_large_single_full_size(mode):
     """The benchmark's workload, in the benchmark's launch configuration: V from
     the deviations on the device (every 4th row, 1/sqrt(Nens-1)), then the
