@@ -65,6 +65,7 @@ struct PanelArgs {
     int32_t rows_per_blk;
     int32_t panel_b;
     int32_t check;
+    int32_t vec_ok;                // 16-byte aligned columns (U, Z, V) and row blocks
     uint64_t timeout_ns;
 };
 

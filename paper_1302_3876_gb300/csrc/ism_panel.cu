@@ -32,6 +32,7 @@ constexpr int kPB = 32;     // largest panel width
 constexpr int RT = 64;      // rows per tile
 constexpr int CT = 64;      // columns per tile
 constexpr int XLD = RT + 4; // padded tile stride (keeps 16-byte alignment)
+constexpr int kScratch = 256 * 16;   // floats: A tile of W' (kPB*CT) or the GEMM2 row-half combine (256*16)
 
 struct PanelSmem {
     double* G;      // [kPB][kPB]
@@ -137,65 +138,119 @@ __device__ bool reduce_panel(const PanelArgs& a, const PanelSmem& s, int nvals, 
     return grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, s.flag);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Stages rows [row0, row0 + nr) of ncl columns into a [col][XLD] tile (zero fill past nr / ncl).
+// VEC: 16-byte copies (column bases 16-byte aligned and row0 % 4 == 0), else 4-byte copies.
+template <bool VEC, typename ColFn>
+__device__ __forceinline__ void stage_cols(float* dst, int ld, int ncols_tile, int ncl, int64_t row0, int nr, ColFn col) {
+    const int tid = threadIdx.x;
+    if (VEC) {
+        for (int e = tid; e < ncols_tile * (RT / 4); e += kPT) {
+            const int c = e >> 4, j4 = (e & 15) * 4;
+            const int rem = nr - j4;
+            const int bytes = (c < ncl && rem > 0) ? (rem >= 4 ? 16 : 4 * rem) : 0;
+            const float* src = bytes ? col(c) + row0 + j4 : col(0) + row0;   // valid address even when 0 bytes
+            cp_async16(dst + c * ld + j4, src, bytes);
+        }
+    } else {
+        for (int e = tid; e < ncols_tile * RT; e += kPT) {
+            const int c = e >> 6, j = e & 63;
+            const int bytes = (c < ncl && j < nr) ? 4 : 0;
+            cp_async4(dst + c * ld + j, bytes ? col(c) + row0 + j : col(0) + row0, bytes);
+        }
+    }
+}
+
 // One sweep over this CTA's rows for the panel [k0, k0+bp) (bp = 0: no update) and
 // the next panel [k1, k1+nb) (nb = 0: no dots).  A (reduced dots of the previous
 // sweep) is read from coefg with row stride ncols_prev = ncols + bp.
-__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
-                      int nb) {
+// Thread tiles use interleaved columns (c = x + 16 q) so that the 16-byte shared
+// loads of 16 lanes fall in distinct banks.
+template <bool VEC>
+__device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
+                        int nb) {
     const int N = a.nens;
     const int ncols = (N - k1) + N;
     const int ncols_prev = ncols + bp;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float* V = static_cast<const float*>(a.V);
+    const int ntiles = (int)((nrows + RT - 1) / RT);
+    // GEMM2 mapping: columns cq + 16 q, dot rows tq*4 + s, row half
+    const int cq = tid & 15, tq = (tid >> 4) & 7, half = tid >> 7;
     for (int c0 = 0; c0 < ncols; c0 += CT) {
         const int ncl = min(CT, ncols - c0);
         __syncthreads();
         if (bp > 0) {
-            // W'[t][c] = sum_s W[t][s] A[s][c0 + c + bp]
+            // A tile (float) then W'[t][c] = sum_u W[t][u] A[u][c], stored permuted: Wt[t][x*4+q] = W'[t][x+16q]
+            float* As = s.VNs + 2 * kPB * RT;    // [kPB][CT] scratch after the double-buffered tiles
             for (int e = tid; e < bp * CT; e += kPT) {
-                const int t = e / CT, c = e % CT;
+                const int u = e >> 6, c = e & 63;
+                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]) : 0.f;
+            }
+            __syncthreads();
+            for (int e = tid; e < bp * CT; e += kPT) {
+                const int t = e >> 6, c = e & 63;
                 float v = 0.f;
-                if (c < ncl)
-                    for (int u = 0; u < bp; ++u)
-                        v = fmaf(s.W[t * kPB + u], (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]), v);
-                s.Wt[t * CT + c] = v;
+                for (int u = 0; u < bp; ++u) v = fmaf(s.W[t * kPB + u], As[u * CT + c], v);
+                s.Wt[t * CT + (c & 15) * 4 + (c >> 4)] = v;
             }
         }
-        // GEMM2 accumulators: thread -> column c = tid % 64, rows of A' t = tg + 4 q
-        const int gc = tid & 63, tg = tid >> 6;
-        float acc[kPB / 4], outer[kPB / 4];
+        float acc[4][4];
 #pragma unroll
-        for (int q = 0; q < kPB / 4; ++q) acc[q] = 0.f, outer[q] = 0.f;
-        for (int64_t rr = 0; rr < nrows; rr += RT) {
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
+        auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
+        auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
+        auto vcol = [&](int t) { return V + (int64_t)(k1 + t) * a.ldv; };
+        auto stage = [&](int tile, int buf) {
+            const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
+            float* xs = s.Xs + buf * CT * XLD;
+            stage_cols<VEC>(xs, XLD, CT, ncl, row0, nr, xcol);
+            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
+            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
+            cp_async_commit();
+        };
+        __syncthreads();
+        stage(0, 0);
+        for (int tile = 0; tile < ntiles; ++tile) {
+            const int buf = tile & 1;
+            if (tile + 1 < ntiles) {
+                stage(tile + 1, buf ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
             __syncthreads();
-            // stage X tile (columns c0.., rows row0..), U_P and V_{P'} tiles
-            for (int e = tid; e < CT * RT; e += kPT) {
-                const int c = e / RT, j = e % RT;
-                float v = 0.f;
-                if (c < ncl && j < nr) v = col_ptr(a, trail_col(c0 + c, N, k1))[row0 + j];
-                s.Xs[c * XLD + j] = v;
-            }
-            for (int e = tid; e < bp * RT; e += kPT) {
-                const int t = e / RT, j = e % RT;
-                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
-            }
-            for (int e = tid; e < nb * RT; e += kPT) {
-                const int t = e / RT, j = e % RT;
-                s.VNs[t * RT + j] = j < nr ? V[(int64_t)(k1 + t) * a.ldv + row0 + j] : 0.f;
-            }
-            __syncthreads();
+            float* xs = s.Xs + buf * CT * XLD;
+            const float* ups = s.UPs + buf * kPB * RT;
+            const float* vns = s.VNs + buf * kPB * RT;
+            const int64_t rr = (int64_t)tile * RT;
+            const int nr = (int)min((int64_t)RT, nrows - rr);
             if (bp > 0) {
-                // GEMM1: thread (ty, tx) -> rows 4 ty.., columns 4 tx..
+                // GEMM1: rows 4 ty.., columns tx + 16 q
                 float x[4][4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 v = *reinterpret_cast<const float4*>(&s.Xs[(tx * 4 + q) * XLD + ty * 4]);
+                    const float4 v = *reinterpret_cast<const float4*>(&xs[(tx + 16 * q) * XLD + ty * 4]);
                     x[0][q] = v.x, x[1][q] = v.y, x[2][q] = v.z, x[3][q] = v.w;
                 }
+#pragma unroll 4
                 for (int t = 0; t < bp; ++t) {
-                    const float4 u = *reinterpret_cast<const float4*>(&s.UPs[t * RT + ty * 4]);
+                    const float4 u = *reinterpret_cast<const float4*>(&ups[t * RT + ty * 4]);
                     const float4 w = *reinterpret_cast<const float4*>(&s.Wt[t * CT + tx * 4]);
                     const float uu[4] = {u.x, u.y, u.z, u.w}, ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -203,40 +258,68 @@ __device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_
 #pragma unroll
                         for (int q = 0; q < 4; ++q) x[i][q] = fmaf(-uu[i], ww[q], x[i][q]);
                 }
-                __syncthreads();
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<float4*>(&s.Xs[(tx * 4 + q) * XLD + ty * 4]) =
+                    *reinterpret_cast<float4*>(&xs[(tx + 16 * q) * XLD + ty * 4]) =
                         make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
                 __syncthreads();
-                // write the updated tile back (coalesced 64-row segments)
-                for (int e = tid; e < CT * RT; e += kPT) {
-                    const int c = e / RT, j = e % RT;
-                    if (c < ncl && j < nr) col_ptr(a, trail_col(c0 + c, N, k1))[row0 + j] = s.Xs[c * XLD + j];
-                }
-            }
-            if (nb > 0) {
-                // GEMM2: A'[t][gc] += sum_j VN[t][j] X[gc][j]
-                for (int j = 0; j < RT; j += 4) {
-                    const float4 xv = *reinterpret_cast<const float4*>(&s.Xs[gc * XLD + j]);
-#pragma unroll
-                    for (int q = 0; q < kPB / 4; ++q) {
-                        const int t = tg + 4 * q;
-                        if (t < nb) {
-                            const float4 vv = *reinterpret_cast<const float4*>(&s.VNs[t * RT + j]);
-                            acc[q] = fmaf(vv.x, xv.x, fmaf(vv.y, xv.y, fmaf(vv.z, xv.z, fmaf(vv.w, xv.w, acc[q]))));
-                        }
+                // write the updated tile back: 16-byte stores along rows
+                for (int e = tid; e < CT * (RT / 4); e += kPT) {
+                    const int c = e >> 4, j4 = (e & 15) * 4;
+                    if (c >= ncl) continue;
+                    float* dst = xcol(c) + r0 + rr + j4;
+                    const float4 v = *reinterpret_cast<const float4*>(&xs[c * XLD + j4]);
+                    if (VEC && j4 + 4 <= nr) {
+                        *reinterpret_cast<float4*>(dst) = v;
+                    } else {
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+                        for (int q = 0; q < 4; ++q)
+                            if (j4 + q < nr) dst[q] = vv[q];
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < kPB / 4; ++q) outer[q] += acc[q], acc[q] = 0.f;
             }
-        }
-        if (nb > 0 && gc < ncl) {
+            if (nb > 0 && tq * 4 < nb) {
+                // GEMM2: acc[s][q] += sum_j VN[tq*4+s][j] X[cq+16q][j] over this thread's row half
+                const int jb = half * (RT / 2);
+#pragma unroll 2
+                for (int j = jb; j < jb + RT / 2; j += 4) {
+                    float4 xv[4], vv[4];
 #pragma unroll
-            for (int q = 0; q < kPB / 4; ++q) {
-                const int t = tg + 4 * q;
-                if (t < nb) __stcg(&a.part[(int64_t)blockIdx.x * a.part_stride + t * ncols + c0 + gc], (double)outer[q]);
+                    for (int q = 0; q < 4; ++q) xv[q] = *reinterpret_cast<const float4*>(&xs[(cq + 16 * q) * XLD + j]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) vv[q] = *reinterpret_cast<const float4*>(&vns[(tq * 4 + q) * RT + j]);
+#pragma unroll
+                    for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            acc[s4][q] = fmaf(vv[s4].x, xv[q].x, fmaf(vv[s4].y, xv[q].y,
+                                         fmaf(vv[s4].z, xv[q].z, fmaf(vv[s4].w, xv[q].w, acc[s4][q]))));
+                }
+            }
+            __syncthreads();     // the buffer is refilled by the next iteration's prefetch
+        }
+        if (nb > 0) {
+            // combine the two row halves in a fixed order, then write this CTA's partial
+            float* red = s.VNs + 2 * kPB * RT;   // [256][16] scratch
+            __syncthreads();
+            if (half == 1)
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) red[(tid - 128) * 16 + s4 * 4 + q] = acc[s4][q];
+            __syncthreads();
+            if (half == 0 && tq * 4 < nb) {
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const int t = tq * 4 + s4;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = cq + 16 * q;
+                        if (t < nb && c < ncl)
+                            __stcg(&a.part[(int64_t)blockIdx.x * a.part_stride + t * ncols + c0 + c],
+                                   (double)(acc[s4][q] + red[tid * 16 + s4 * 4 + q]));
+                    }
+                }
             }
         }
     }
@@ -247,12 +330,12 @@ __device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_
             const int64_t row0 = r0 + rr;
             __syncthreads();
             for (int e = tid; e < bp * RT; e += kPT) {
-                const int t = e / RT, j = e % RT;
+                const int t = e >> 6, j = e & 63;
                 s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
             }
             __syncthreads();
             for (int e = tid; e < bp * RT; e += kPT) {
-                const int m = e / RT, j = e % RT;
+                const int m = e >> 6, j = e & 63;
                 float v = 0.f;
                 for (int u = 0; u <= m; ++u) v = fmaf(s.UPs[u * RT + j], s.Bf[u * kPB + m], v);
                 if (j < nr) col_ptr(a, k0 + m)[row0 + j] = v;
@@ -261,22 +344,33 @@ __device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_
     }
 }
 
+__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
+                      int nb) {
+    if (a.vec_ok)
+        sweep_t<true>(a, s, r0, nrows, k0, bp, k1, nb);
+    else
+        sweep_t<false>(a, s, r0, nrows, k0, bp, k1, nb);
+}
+
 __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // persistent: L, gamma, W, Bf, W'; tile buffers; the factor's temporaries G, beta, B
+    // alias the X tile buffers (they are dead between sweeps)
     PanelSmem s;
-    s.G = reinterpret_cast<double*>(smem_raw);
-    s.beta = s.G + kPB * kPB;
-    s.Bm = s.beta + kPB * kPB;
-    s.L = s.Bm + kPB * kPB;
+    s.L = reinterpret_cast<double*>(smem_raw);
     s.gam = s.L + kPB * kPB;
     s.red = s.gam + kPB;
     s.W = reinterpret_cast<float*>(s.red + 32);
     s.Bf = s.W + kPB * kPB;
     s.Wt = s.Bf + kPB * kPB;
     s.Xs = s.Wt + kPB * CT;
-    s.UPs = s.Xs + CT * XLD;
-    s.VNs = s.UPs + kPB * RT;
-    s.flag = reinterpret_cast<int*>(s.VNs + kPB * RT);
+    s.UPs = s.Xs + 2 * CT * XLD;
+    s.VNs = s.UPs + 2 * kPB * RT;
+    s.flag = reinterpret_cast<int*>(s.VNs + 2 * kPB * RT + kScratch);
+    s.G = reinterpret_cast<double*>(s.Xs);
+    s.beta = s.G + kPB * kPB;
+    s.Bm = s.beta + kPB * kPB;
+    static_assert(3 * kPB * kPB * sizeof(double) <= 2 * CT * XLD * sizeof(float), "factor temporaries fit the tiles");
 
     const int N = a.nens, b = a.panel_b;
     const int tid = threadIdx.x;
@@ -355,8 +449,8 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
 }
 
 size_t panel_smem() {
-    return sizeof(double) * (4 * kPB * kPB + kPB + 32) + sizeof(float) * (2 * kPB * kPB + kPB * CT + CT * XLD +
-                                                                          2 * kPB * RT) + 16;
+    return sizeof(double) * (kPB * kPB + kPB + 32) +
+           sizeof(float) * (2 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
 }
 
 }  // namespace
