@@ -50,6 +50,24 @@ def level_bytes(nobs, nens, w):
     return w * nobs * (3 * nens * nens + 5 * nens)
 
 
+def panel_bytes(nobs, nens, b, w):
+    """Algorithmic bytes of one panel-kernel launch: the first pass reads the 2N columns
+    of [U | Z] and b columns of V; panel p (start k0) reads and writes its 2N - k0 - b
+    trailing columns, reads the b panel columns of U and the next b columns of V, and
+    rewrites the b panel columns with their final values."""
+    cols = 2 * nens + b
+    for k0 in range(0, nens, b):
+        bp = min(b, nens - k0)
+        nb = min(b, max(0, nens - k0 - bp))
+        cols += 2 * (2 * nens - k0 - bp) + bp + nb + 2 * bp
+    return w * nobs * cols
+
+
+def fp32_alu_peak_tflops(sm_count=152, lanes=128, mhz=2070.0):
+    """FP32 CUDA-core peak: SMs x FP32 lanes per SM x 2 flop per FMA x clock."""
+    return sm_count * lanes * 2 * mhz * 1e6 / 1e12
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -59,10 +77,10 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_src: str, workload_key: str):
+def profile_traffic(kernel_src: str, summary_name: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
     current source of the kernel (sha256 recorded in the summary)."""
-    path = os.path.join(ROOT, "profiles", f"ism_levels_{workload_key}.md")
+    path = os.path.join(ROOT, "profiles", summary_name)
     try:
         text = open(path).read()
         sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
@@ -327,8 +345,28 @@ def run_ours(args):
     peak, peak_kind = read_peaks()
     lv_ms, lv_n = phases.get("ism_solve", (float("nan"), 0))
     lv_avg = lv_ms / max(lv_n, 1)
-    lb = level_bytes(NOBS, NENS, 4)
-    achieved = lb / (lv_avg / 1e3) / 1e9
+    src_dir = os.path.join(ROOT, "paper_1302_3876_gb300", "csrc")
+    if args.mode == "fp32":
+        lb = level_bytes(NOBS, NENS, 4)
+        achieved = lb / (lv_avg / 1e3) / 1e9
+        roofline = {"kernel": "ism_levels_kernel<float,4>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                    "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
+                    "traffic": profile_traffic(os.path.join(src_dir, "ism_stream.cu"),
+                                               "ism_levels_large_single_fp32.md")}
+    else:
+        f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
+        achieved = f_solve / (lv_avg / 1e3) / 1e12
+        alu_peak = fp32_alu_peak_tflops()
+        pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
+        roofline = {"kernel": "ism_panel_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)",
+                    "algorithmic_flops_per_launch": f_solve, "avg_launch_ms": lv_avg,
+                    "hbm_view": {"algorithmic_bytes_per_launch": pb, "achieved_gbs": pb / (lv_avg / 1e3) / 1e9,
+                                 "peak_gbs": peak, "frac": pb / (lv_avg / 1e3) / 1e9 / peak},
+                    "traffic": profile_traffic(os.path.join(src_dir, "ism_panel.cu"),
+                                               "ism_panel_large_single_fp32.md")}
     total_ms = sum(v[0] for v in phases.values())
     ms_step = t_max / args.steps
     line = {
@@ -336,20 +374,17 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nstate": NSTATE, "nobs": NOBS, "nens": NENS,
-                   "path": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)",
+                   "path": ("panel form on FP32 CUDA cores, b=%d (FP64 gamma)" % args.panel_b
+                            if args.mode == "panel32" else "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"),
                    "l2": "inputs 1.3 GB > L2; no flush", "parallelism": f"replicas x{world}"},
         "gflops": flops(NSTATE, NOBS, NENS) / (ms_step / 1e3) / 1e9,
         "gamma_min": inf.gamma_min, "gamma_max": inf.gamma_max,
-        "roofline": {"kernel": "ism_levels_kernel<float,4>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
-                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
-                     "traffic": profile_traffic(os.path.join(ROOT, "paper_1302_3876_gb300", "csrc", "ism_stream.cu"),
-                                                "large_single_fp32")},
+        "roofline": roofline,
         "phases_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in phases.items()},
         "phase_share": {k: v[0] / total_ms for k, v in phases.items()} if total_ms > 0 else {},
         "e2e": {"value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,   # prep, solve, Gram (2), M, split of M, X_A
         "clocks": clk.summary(),
         "comparator_fp64": fp64,
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},

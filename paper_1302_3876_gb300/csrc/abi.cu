@@ -54,7 +54,8 @@ struct enkf_ism_plan_s {
     int32_t nsplit;
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
-    size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, total;
+    size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
+        total;
     // latched status of the previous call
     int* h_status;            // pinned host word
     cudaEvent_t done;
@@ -161,6 +162,7 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_Q = o; o = align256(o + sizeof(double) * N * N);
     p->off_M = o; o = align256(o + p->w * N * N);
     p->off_M64 = o; o = align256(o + sizeof(double) * N * N);
+    p->off_Msplit = o; o = align256(o + 2 * sizeof(uint16_t) * N * (size_t)xa_tc_kpad(nens));
     p->total = o;
     e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
@@ -355,7 +357,12 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         prof_end(p, slot, s);
         if (dXB) {
             slot = prof_begin(p, 4, s);
-            CU(xa_update(p->fp64, p->nstate, p->nens, XB, ldb, dXB, ldx, Mp, XA, lda, s), "xa_update launch");
+            if (p->fp64)
+                CU(xa_update(true, p->nstate, p->nens, XB, ldb, dXB, ldx, Mp, XA, lda, s), "xa_update launch");
+            else
+                CU(xa_update_tc(p->nstate, p->nens, (const float*)XB, ldb, (const float*)dXB, ldx, (const float*)Mp,
+                                ws + p->off_Msplit, (float*)XA, lda, s),
+                   "xa_update_tc launch");
             prof_end(p, slot, s);
         }
     }

@@ -61,51 +61,55 @@ __device__ __forceinline__ int trail_col(int a, int N, int k1) {
     return a < nu ? k1 + a : N + (a - nu);
 }
 
-// b x b factor from G (FP64), by one warp; lanes own columns j (j, j + 32, ...).
+// b x b factor from the panel Gram G by one warp; lanes own columns j.  The level
+// denominators gamma_m = 1 + (G beta_m)_m are formed in FP64 from the FP64 Gram;
+// the coefficient vectors beta, B, L and W are carried in FP32 (they only scale
+// FP32 updates; FP64 work on them would occupy the narrow FP64 pipe for ~60 us
+// per panel).
 __device__ void factor_warp(const PanelSmem& s, int bp) {
     const int lane = threadIdx.x & 31;
+    float* beta = reinterpret_cast<float*>(s.beta);    // [kPB][kPB] float view of the FP64 scratch
+    float* Bm = reinterpret_cast<float*>(s.Bm);
+    float* Gf = reinterpret_cast<float*>(s.Bm) + kPB * kPB;
+    for (int e = lane; e < bp * kPB; e += 32) Gf[e] = (float)s.G[e];
+    __syncwarp();
     for (int m = 0; m < bp; ++m) {
-        double gm[kPB / 32 + 1];
-        int cnt = 0;
-        for (int j = lane; j < bp; j += 32, ++cnt) {
-            double v = 0.0;
-            if (j >= m)
-                for (int u = 0; u < bp; ++u) v += s.G[m * kPB + u] * s.beta[u * kPB + j];
-            gm[cnt] = v;
-        }
-        // (G beta_m)_m lives on lane m % 32, slot m / 32
-        double mine = gm[0];
-        for (int q = 1; q <= (bp - 1) / 32; ++q)
-            if ((m >> 5) == q) mine = gm[q];
-        const double gmm = __shfl_sync(0xffffffffu, mine, m & 31);
+        const int j = lane;
+        float gm = 0.f;
+        if (j >= m && j < bp)
+            for (int u = 0; u < bp; ++u) gm = fmaf(Gf[m * kPB + u], beta[u * kPB + j], gm);
+        // gamma_m in FP64: 1 + sum_u G[m][u] beta[u][m]
+        double gmm = 0.0;
+        if (lane == 0)
+            for (int u = 0; u < bp; ++u) gmm += s.G[m * kPB + u] * (double)beta[u * kPB + m];
+        gmm = __shfl_sync(0xffffffffu, gmm, 0);
         const double gam = 1.0 + gmm;
         if (lane == 0) s.gam[m] = gam;
-        for (int u = lane; u < bp; u += 32) s.Bm[u * kPB + m] = s.beta[u * kPB + m] / gam;
+        const float ginv = (float)(1.0 / gam);
+        if (lane < bp) Bm[lane * kPB + m] = beta[lane * kPB + m] * ginv;
         __syncwarp();
-        cnt = 0;
-        for (int j = lane; j < bp; j += 32, ++cnt)
-            if (j > m)
-                for (int u = 0; u < bp; ++u) s.beta[u * kPB + j] -= s.Bm[u * kPB + m] * gm[cnt];
+        if (j > m && j < bp)
+            for (int u = 0; u < bp; ++u) beta[u * kPB + j] = fmaf(-Bm[u * kPB + m], gm, beta[u * kPB + j]);
         __syncwarp();
     }
     for (int m = 0; m < bp; ++m) {
-        for (int l = lane; l < bp; l += 32) {
-            double v = 0.0;
-            if (l < m)
-                for (int u = 0; u < bp; ++u) v += s.G[m * kPB + u] * s.Bm[u * kPB + l];
-            s.L[m * kPB + l] = (l < m) ? v : 0.0;
-        }
+        const int l = lane;
+        float v = 0.f;
+        if (l < m)
+            for (int u = 0; u < bp; ++u) v = fmaf(Gf[m * kPB + u], Bm[u * kPB + l], v);
+        if (l < bp) s.L[m * kPB + l] = (l < m) ? (double)v : 0.0;
     }
     __syncwarp();
-    for (int q = lane; q < bp; q += 32) {
-        double wr[kPB];
+    if (lane < bp) {
+        const int q = lane;
+        float wr[kPB];
         for (int l = bp - 1; l >= 0; --l) {
-            double v = s.Bm[q * kPB + l];
-            for (int m = l + 1; m < bp; ++m) v -= s.L[m * kPB + l] * wr[m];
+            float v = Bm[q * kPB + l];
+            for (int m = l + 1; m < bp; ++m) v = fmaf(-(float)s.L[m * kPB + l], wr[m], v);
             wr[l] = v;
-            s.W[q * kPB + l] = (float)v;
+            s.W[q * kPB + l] = v;
         }
-        for (int m = 0; m < bp; ++m) s.Bf[q * kPB + m] = (float)(s.Bm[q * kPB + m] * s.gam[m]);
+        for (int m = 0; m < bp; ++m) s.Bf[q * kPB + m] = (float)((double)Bm[q * kPB + m] * s.gam[m]);
     }
     __syncwarp();
 }
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
         for (int e = tid; e < bp * bp; e += kPT) {
             const int t = e / bp, u = e % bp;
             s.G[t * kPB + u] = __ldcg(&a.coefg[t * ncols_prev + u]);
-            s.beta[t * kPB + u] = (t == u) ? 1.0 : 0.0;
+            reinterpret_cast<float*>(s.beta)[t * kPB + u] = (t == u) ? 1.f : 0.f;
         }
         __syncthreads();
         if (tid < 32) factor_warp(s, bp);
@@ -419,12 +423,12 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
             if (tid < bp) a.gamma[k0 + tid] = s.gam[tid];
             for (int i = tid; i < N; i += kPT) {
                 const int ai = (N - k0) + i;   // index of z_i among the previous sweep's columns
-                double c[kPB];
+                float c[kPB];
                 for (int m = 0; m < bp; ++m) {
-                    double v = __ldcg(&a.coefg[m * ncols_prev + ai]);
-                    for (int l = 0; l < m; ++l) v -= s.L[m * kPB + l] * c[l];
+                    float v = (float)__ldcg(&a.coefg[m * ncols_prev + ai]);
+                    for (int l = 0; l < m; ++l) v = fmaf(-(float)s.L[m * kPB + l], c[l], v);
                     c[m] = v;
-                    a.C[(int64_t)(k0 + m) * N + i] = v;
+                    a.C[(int64_t)(k0 + m) * N + i] = (double)v;
                 }
             }
             if (a.check && tid == 0) {
