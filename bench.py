@@ -68,6 +68,14 @@ def fp32_alu_peak_tflops(sm_count=152, lanes=128, mhz=2070.0):
     return sm_count * lanes * 2 * mhz * 1e6 / 1e12
 
 
+def read_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:  # noqa: BLE001
+        return 1900.0
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -248,8 +256,9 @@ def run_ours(args):
     V = torch.empty(NENS, NOBS, dtype=torch.float32, device=dev)
     XA = torch.empty_like(dX)
     M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
-    mode = enkf.ENKF_PANEL_FP32 if args.mode == "panel32" else enkf.ENKF_FP32
-    plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode == "panel32" else 0, device=dev)
+    mode = {"panel32": enkf.ENKF_PANEL_FP32, "bf16": enkf.ENKF_PANEL_BF16, "fp16": enkf.ENKF_PANEL_FP16,
+            "fp32": enkf.ENKF_FP32}[args.mode]
+    plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode != "fp32" else 0, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -354,6 +363,23 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_stream.cu"),
                                                "ism_levels_large_single_fp32.md")}
+    elif args.mode in ("bf16", "fp16"):
+        f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
+        pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
+        achieved = pb / (lv_avg / 1e3) / 1e9
+        mult = 3 if args.mode == "bf16" else 1            # split operands: three tensor products
+        bf16_peak = read_bf16_peak()
+        roofline = {"kernel": "ism_panel_kernel<%d>" % (1 if args.mode == "bf16" else 2), "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)", "algorithmic_bytes_per_launch": pb,
+                    "avg_launch_ms": lv_avg,
+                    "tensor_view": {"tensor_flops_per_launch": mult * f_solve,
+                                    "achieved_tflops": mult * f_solve / (lv_avg / 1e3) / 1e12,
+                                    "peak_tflops": bf16_peak,
+                                    "frac": mult * f_solve / (lv_avg / 1e3) / 1e12 / bf16_peak,
+                                    "note": "mma.sync m16n8k16; fp16 and bf16 share the dense peak"},
+                    "traffic": profile_traffic(os.path.join(src_dir, "ism_panel.cu"),
+                                               f"ism_panel_large_single_{args.mode}.md")}
     else:
         f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
         achieved = f_solve / (lv_avg / 1e3) / 1e12
@@ -374,8 +400,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nstate": NSTATE, "nobs": NOBS, "nens": NENS,
-                   "path": ("panel form on FP32 CUDA cores, b=%d (FP64 gamma)" % args.panel_b
-                            if args.mode == "panel32" else "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"),
+                   "path": {"panel32": "panel form on FP32 CUDA cores, b=%d (FP64 gamma)" % args.panel_b,
+                            "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)" % args.panel_b,
+                            "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)" % args.panel_b,
+                            "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}[args.mode],
                    "l2": "inputs 1.3 GB > L2; no flush", "parallelism": f"replicas x{world}"},
         "gflops": flops(NSTATE, NOBS, NENS) / (ms_step / 1e3) / 1e9,
         "gamma_min": inf.gamma_min, "gamma_max": inf.gamma_max,
@@ -403,8 +431,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["panel32", "fp32"], default="panel32",
-                    help="headline path: panel form on FP32 CUDA cores, or the FP32 level-streaming path")
+    ap.add_argument("--mode", choices=["panel32", "bf16", "fp16", "fp32"], default="panel32",
+                    help="headline path: panel form on FP32 CUDA cores (panel32), on tensor cores with split BF16 "
+                         "(bf16) or FP16 (fp16) operands, or the FP32 level-streaming path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
     ap.add_argument("--scale-div", type=int, default=1,
                     help="divide Nobs and Nstate by this factor (small case for profiler captures)")

@@ -69,8 +69,10 @@ typedef enum {
 typedef enum {
     ENKF_FP64 = 0,        /* plain level-by-level path, double storage and arithmetic */
     ENKF_FP32 = 1,        /* plain level-by-level path, float storage, double gamma */
-    ENKF_PANEL_BF16 = 2,  /* panel form, bf16 tensor-core trailing updates, FP64 denominators */
-    ENKF_PANEL_FP16 = 3,  /* panel form, fp16 tensor-core trailing updates, FP64 denominators */
+    ENKF_PANEL_BF16 = 2,  /* panel form, tensor-core trailing updates and dots with split BF16 operands
+                             (x = hi + lo, three products), FP32 storage/accumulation, FP64 denominators */
+    ENKF_PANEL_FP16 = 3,  /* panel form, tensor-core trailing updates and dots in one FP16 product,
+                             FP32 storage/accumulation, FP64 denominators */
     ENKF_PANEL_FP32 = 4   /* panel form on FP32 CUDA cores (b levels per pass), FP64 denominators */
 } enkf_mode;
 
@@ -102,8 +104,8 @@ typedef struct {
  *                    the solve only (M and X_A need nens >= 2, since S divides
  *                    by sqrt(Nens - 1)).
  *   mode             an enkf_mode.
- *   panel_b          panel width for the panel modes (0 = default 32; ENKF_PANEL_FP32 takes
- *                    1 <= panel_b <= 32); ignored otherwise.
+ *   panel_b          panel width for the panel modes (0 = default 32; 1 <= panel_b <= 32);
+ *                    ignored otherwise.
  *   flags            ENKF_FLAG_* bits.
  *   workspace_bytes  receives the device workspace size enkf_ism_analysis needs.
  *

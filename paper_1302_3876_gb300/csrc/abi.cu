@@ -112,12 +112,9 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     if (nens > 1024) return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: nens %d > 1024", nens);
     if (nobs > ((int64_t)1 << 40) || nstate > ((int64_t)1 << 40))
         return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: size too large");
-    if (mode != ENKF_FP64 && mode != ENKF_FP32 && mode != ENKF_PANEL_FP32) {
-        if (mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16)
-            return fail(ENKF_ERR_UNSUPPORTED, "enkf_ism_plan: tensor-core panel modes are not built yet");
-        return fail(ENKF_ERR_ARG, "enkf_ism_plan: bad mode %d", mode);
-    }
-    if (mode == ENKF_PANEL_FP32 && (panel_b < 0 || panel_b > panel_max_b()))
+    const bool panel = (mode == ENKF_PANEL_FP32 || mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16);
+    if (mode != ENKF_FP64 && mode != ENKF_FP32 && !panel) return fail(ENKF_ERR_ARG, "enkf_ism_plan: bad mode %d", mode);
+    if (panel && (panel_b < 0 || panel_b > panel_max_b()))
         return fail(ENKF_ERR_ARG, "enkf_ism_plan: panel_b %d out of [1, %d]", panel_b, panel_max_b());
     if (flags & ~(ENKF_FLAG_REFINE | ENKF_FLAG_NO_CHECKS | ENKF_FLAG_TEST_TIMEOUT))
         return fail(ENKF_ERR_ARG, "enkf_ism_plan: unknown flag bits 0x%x", flags);
@@ -127,14 +124,15 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->nobs = nobs;
     p->nens = nens;
     p->mode = mode;
-    p->panel_b = (mode == ENKF_PANEL_FP32) ? (panel_b > 0 ? panel_b : panel_max_b()) : 0;
+    p->panel_b = panel ? (panel_b > 0 ? panel_b : panel_max_b()) : 0;
     p->flags = flags;
     p->fp64 = (mode == ENKF_FP64);
     p->w = p->fp64 ? 8 : 4;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) {
-        if (mode == ENKF_PANEL_FP32) {
-            e = panel_plan(nobs, nens, p->panel_b, &p->P);
+        if (panel) {
+            const int prec = mode == ENKF_PANEL_BF16 ? 1 : mode == ENKF_PANEL_FP16 ? 2 : 0;
+            e = panel_plan(nobs, nens, p->panel_b, prec, &p->P);
             p->L.grid = p->P.grid;
         } else {
             e = level_plan(p->fp64, nobs, nens, &p->L);
@@ -152,8 +150,8 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_ctl = o; o = align256(o + sizeof(Control));
     p->off_U = o; o = align256(o + p->w * (size_t)p->ldu * N);
     p->off_Z = o; o = align256(o + p->w * (size_t)p->ldzw * N);
-    const size_t part_per_cta = (mode == ENKF_PANEL_FP32) ? (size_t)p->P.part_stride : 2 * N;
-    const size_t coef_len = (mode == ENKF_PANEL_FP32) ? (size_t)p->P.part_stride : 2 * N;
+    const size_t part_per_cta = panel ? (size_t)p->P.part_stride : 2 * N;
+    const size_t coef_len = panel ? (size_t)p->P.part_stride : 2 * N;
     p->off_part = o; o = align256(o + sizeof(double) * (size_t)p->L.grid * part_per_cta);
     p->off_coefg = o; o = align256(o + sizeof(double) * coef_len);
     p->off_C = o; o = align256(o + sizeof(double) * N * N);
@@ -314,7 +312,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     a.test_skip_arrival = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 1 : 0;
     a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
     int slot = prof_begin(p, 1, s);
-    if (p->mode == ENKF_PANEL_FP32) {
+    if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16) {
         PanelArgs pa;
         pa.nobs = p->nobs;
         pa.nens = p->nens;

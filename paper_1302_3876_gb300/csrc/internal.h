@@ -75,11 +75,12 @@ struct PanelLaunch {
     size_t smem;
     int rows_per_blk;
     int b;
+    int prec;                      // 0 FP32 CUDA cores, 1 BF16 split tensor cores, 2 FP16 tensor cores
     int64_t part_stride;
 };
 
 int panel_max_b();
-cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, PanelLaunch* out);
+cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, PanelLaunch* out);
 cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
 
 // Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,

@@ -20,6 +20,8 @@
 // update GEMM X -= U_P W' (K = b) and the next panel's dots A' += V_{P'}^T X_new
 // (K = rows), both register-tiled from shared memory.  A' partials are reduced
 // across CTAs in a fixed order between two bounded grid barriers.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "internal.h"
@@ -48,7 +50,14 @@ struct PanelSmem {
     float* UPs;     // [kPB][RT]
     float* VNs;     // [kPB][RT]
     int* flag;      // [4]
+    // tensor-core variants: 16-bit operand tiles (hi, and lo for the split form)
+    unsigned short *Uh, *Ul;   // [kPB][HP]   -U_P, [t][row]
+    unsigned short *Wh, *Wl;   // [CT][WPT]   W',   [col][t]
+    unsigned short *Xh, *Xl;   // [CT][HP]    X,    [col][row]
+    unsigned short *Vh, *Vl;   // [kPB][HP]   V',   [t][row]
 };
+constexpr int HP = RT + 8;     // 16-bit tile pitch along rows
+constexpr int WPT = kPB + 8;   // 16-bit tile pitch along t
 
 __device__ __forceinline__ float* col_ptr(const PanelArgs& a, int c) {
     return c < a.nens ? static_cast<float*>(a.U) + (int64_t)c * a.ldu
@@ -348,14 +357,296 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
     }
 }
 
-__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
-                      int nb) {
-    if (a.vec_ok)
-        sweep_t<true>(a, s, r0, nrows, k0, bp, k1, nb);
-    else
-        sweep_t<false>(a, s, r0, nrows, k0, bp, k1, nb);
+// ---------------------------------------------------------------------------
+// Tensor-core sweep (mma.sync m16n8k16, FP32 accumulation).  PREC 1: BF16 split
+// operands (x = hi + lo, three products hi*hi + hi*lo + lo*hi); PREC 2: FP16,
+// one product.  Same data flow as the FP32 sweep; the two GEMMs of a 64 x 64 tile:
+//   GEMM1  X <- X + (-U_P) W'      (M = rows, N = columns, K = t), accumulators start at X
+//   GEMM2  A' += V'^T X_new        (M = t, N = columns, K = rows), accumulators persist
+// ---------------------------------------------------------------------------
+template <int PREC>
+struct Tc;
+template <>
+struct Tc<1> {
+    static constexpr bool split = true;
+    static __device__ __forceinline__ unsigned short hi(float x) { return __bfloat16_as_ushort(__float2bfloat16(x)); }
+    static __device__ __forceinline__ float back(unsigned short h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+    static __device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+};
+template <>
+struct Tc<2> {
+    static constexpr bool split = false;
+    static __device__ __forceinline__ unsigned short hi(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    static __device__ __forceinline__ float back(unsigned short h) { return __half2float(__ushort_as_half(h)); }
+    static __device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
+};
+
+__device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t* r, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm2(uint32_t* r, const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
 
+// hi (and lo) of 4 floats stored as 4 consecutive 16-bit values
+template <int PREC>
+__device__ __forceinline__ void put4(unsigned short* h, unsigned short* l, float4 v) {
+    const float f[4] = {v.x, v.y, v.z, v.w};
+    __align__(8) unsigned short hh[4], ll[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        hh[q] = Tc<PREC>::hi(f[q]);
+        if (Tc<PREC>::split) ll[q] = Tc<PREC>::hi(f[q] - Tc<PREC>::back(hh[q]));
+    }
+    *reinterpret_cast<uint2*>(h) = *reinterpret_cast<const uint2*>(hh);
+    if (Tc<PREC>::split) *reinterpret_cast<uint2*>(l) = *reinterpret_cast<const uint2*>(ll);
+}
+
+template <bool VEC, int PREC>
+__device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
+                         int nb) {
+    constexpr bool SPLIT = Tc<PREC>::split;
+    const int N = a.nens;
+    const int ncols = (N - k1) + N;
+    const int ncols_prev = ncols + bp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float* V = static_cast<const float*>(a.V);
+    const int ntiles = (int)((nrows + RT - 1) / RT);
+    const int j8 = lane >> 3;
+    for (int c0 = 0; c0 < ncols; c0 += CT) {
+        const int ncl = min(CT, ncols - c0);
+        __syncthreads();
+        if (bp > 0) {
+            float* As = s.VNs + 2 * kPB * RT;    // [kPB][CT]
+            for (int e = tid; e < bp * CT; e += kPT) {
+                const int u = e >> 6, c = e & 63;
+                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]) : 0.f;
+            }
+            __syncthreads();
+            // W'[t][c] into [col][t] 16-bit tiles; t >= bp is zero padding of K
+            for (int e = tid; e < kPB * CT; e += kPT) {
+                const int t = e >> 6, c = e & 63;
+                float v = 0.f;
+                if (t < bp)
+                    for (int u = 0; u < bp; ++u) v = fmaf(s.W[t * kPB + u], As[u * CT + c], v);
+                const unsigned short h = Tc<PREC>::hi(v);
+                s.Wh[c * WPT + t] = h;
+                if (SPLIT) s.Wl[c * WPT + t] = Tc<PREC>::hi(v - Tc<PREC>::back(h));
+            }
+        }
+        float acc2[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) acc2[mt][h] = 0.f;
+        auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
+        auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
+        auto vcol = [&](int t) { return V + (int64_t)(k1 + t) * a.ldv; };
+        auto stage = [&](int tile, int buf) {
+            const int64_t rr = (int64_t)tile * RT;
+            const int nr = (int)min((int64_t)RT, nrows - rr);
+            const int64_t row0 = r0 + rr;
+            stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, xcol);
+            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
+            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
+            cp_async_commit();
+        };
+        __syncthreads();
+        stage(0, 0);
+        for (int tile = 0; tile < ntiles; ++tile) {
+            const int buf = tile & 1;
+            if (tile + 1 < ntiles) {
+                stage(tile + 1, buf ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            float* xs = s.Xs + buf * CT * XLD;
+            const float* ups = s.UPs + buf * kPB * RT;
+            const float* vns = s.VNs + buf * kPB * RT;
+            const int64_t rr = (int64_t)tile * RT;
+            const int nr = (int)min((int64_t)RT, nrows - rr);
+            // 16-bit operand tiles: -U_P [t][row], V' [t][row] (zero rows t >= bp / nb)
+            for (int e = tid; e < kPB * (RT / 4); e += kPT) {
+                const int t = e >> 4, r4 = (e & 15) * 4;
+                if (bp > 0) {
+                    float4 u = t < bp ? *reinterpret_cast<const float4*>(&ups[t * RT + r4]) : make_float4(0, 0, 0, 0);
+                    u.x = -u.x, u.y = -u.y, u.z = -u.z, u.w = -u.w;
+                    put4<PREC>(s.Uh + t * HP + r4, s.Ul + t * HP + r4, u);
+                }
+                if (nb > 0) {
+                    const float4 v = t < nb ? *reinterpret_cast<const float4*>(&vns[t * RT + r4]) : make_float4(0, 0, 0, 0);
+                    put4<PREC>(s.Vh + t * HP + r4, s.Vl + t * HP + r4, v);
+                }
+            }
+            if (bp == 0) {
+                for (int e = tid; e < CT * (RT / 4); e += kPT) {
+                    const int c = e >> 4, r4 = (e & 15) * 4;
+                    put4<PREC>(s.Xh + c * HP + r4, s.Xl + c * HP + r4, *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
+                }
+            }
+            __syncthreads();
+            if (bp > 0) {
+                // GEMM1: warp -> rows mt*16.., columns nb0.. (4 n-tiles)
+                const int mt = warp & 3, nb0 = (warp >> 2) * 32;
+                float acc1[4][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int row = mt * 16 + (lane >> 2) + (h >> 1) * 8;
+                        const int col = nb0 + nt * 8 + (lane & 3) * 2 + (h & 1);
+                        acc1[nt][h] = xs[col * XLD + row];
+                    }
+                for (int kk = 0; kk < bp; kk += 16) {
+                    uint32_t ah[4], al[4];
+                    const int kr = kk + (j8 >> 1) * 8 + (lane & 7);
+                    const int mr = mt * 16 + (j8 & 1) * 8;
+                    ldsm4t(ah, s.Uh + kr * HP + mr);
+                    if (SPLIT) ldsm4t(al, s.Ul + kr * HP + mr);
+#pragma unroll
+                    for (int np = 0; np < 2; ++np) {
+                        const int nr2 = nb0 + np * 16 + (j8 >> 1) * 8 + (lane & 7);
+                        const int kc = kk + (j8 & 1) * 8;
+                        uint32_t bh[4], bl[4];
+                        ldsm4(bh, s.Wh + nr2 * WPT + kc);
+                        if (SPLIT) ldsm4(bl, s.Wl + nr2 * WPT + kc);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            float* d = acc1[np * 2 + hh];
+                            if (SPLIT) {
+                                Tc<PREC>::mma(d, al, bh[2 * hh], bh[2 * hh + 1]);
+                                Tc<PREC>::mma(d, ah, bl[2 * hh], bl[2 * hh + 1]);
+                            }
+                            Tc<PREC>::mma(d, ah, bh[2 * hh], bh[2 * hh + 1]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int row = mt * 16 + (lane >> 2) + (h >> 1) * 8;
+                        const int col = nb0 + nt * 8 + (lane & 3) * 2 + (h & 1);
+                        const float v = acc1[nt][h];
+                        xs[col * XLD + row] = v;
+                        const unsigned short hv = Tc<PREC>::hi(v);
+                        s.Xh[col * HP + row] = hv;
+                        if (SPLIT) s.Xl[col * HP + row] = Tc<PREC>::hi(v - Tc<PREC>::back(hv));
+                    }
+                __syncthreads();
+                for (int e = tid; e < CT * (RT / 4); e += kPT) {
+                    const int c = e >> 4, j4 = (e & 15) * 4;
+                    if (c >= ncl) continue;
+                    float* dst = xcol(c) + r0 + rr + j4;
+                    const float4 v = *reinterpret_cast<const float4*>(&xs[c * XLD + j4]);
+                    if (VEC && j4 + 4 <= nr) {
+                        *reinterpret_cast<float4*>(dst) = v;
+                    } else {
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+                        for (int q = 0; q < 4; ++q)
+                            if (j4 + q < nr) dst[q] = vv[q];
+                    }
+                }
+            }
+            if (nb > 0) {
+                // GEMM2: warp -> columns warp*8.. (one n-tile), t = 0..31 (two m-tiles), K = 64 rows
+#pragma unroll
+                for (int kk = 0; kk < RT; kk += 16) {
+                    uint32_t bh[2], bl[2];
+                    const int nrow = warp * 8 + (lane & 7);
+                    const int kc = kk + ((lane >> 3) & 1) * 8;
+                    ldsm2(bh, s.Xh + nrow * HP + kc);
+                    if (SPLIT) ldsm2(bl, s.Xl + nrow * HP + kc);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        if (mt * 16 >= nb) continue;
+                        uint32_t ah[4], al[4];
+                        const int mrow = mt * 16 + (j8 & 1) * 8 + (lane & 7);
+                        const int kcol = kk + (j8 >> 1) * 8;
+                        ldsm4(ah, s.Vh + mrow * HP + kcol);
+                        if (SPLIT) {
+                            ldsm4(al, s.Vl + mrow * HP + kcol);
+                            Tc<PREC>::mma(acc2[mt], al, bh[0], bh[1]);
+                            Tc<PREC>::mma(acc2[mt], ah, bl[0], bl[1]);
+                        }
+                        Tc<PREC>::mma(acc2[mt], ah, bh[0], bh[1]);
+                    }
+                }
+            }
+            __syncthreads();     // the buffers are refilled by the next iteration
+        }
+        if (nb > 0) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int t = mt * 16 + (lane >> 2) + (h >> 1) * 8;
+                    const int c = warp * 8 + (lane & 3) * 2 + (h & 1);
+                    if (t < nb && c < ncl)
+                        __stcg(&a.part[(int64_t)blockIdx.x * a.part_stride + t * ncols + c0 + c], (double)acc2[mt][h]);
+                }
+        }
+    }
+    // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
+    if (bp > 0) {
+        for (int64_t rr = 0; rr < nrows; rr += RT) {
+            const int nr = (int)min((int64_t)RT, nrows - rr);
+            const int64_t row0 = r0 + rr;
+            __syncthreads();
+            for (int e = tid; e < bp * RT; e += kPT) {
+                const int t = e >> 6, j = e & 63;
+                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
+            }
+            __syncthreads();
+            for (int e = tid; e < bp * RT; e += kPT) {
+                const int m = e >> 6, j = e & 63;
+                float v = 0.f;
+                for (int u = 0; u <= m; ++u) v = fmaf(s.UPs[u * RT + j], s.Bf[u * kPB + m], v);
+                if (j < nr) col_ptr(a, k0 + m)[row0 + j] = v;
+            }
+        }
+    }
+}
+
+template <int PREC>
+__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
+                      int nb) {
+    if (PREC == 0) {
+        if (a.vec_ok)
+            sweep_t<true>(a, s, r0, nrows, k0, bp, k1, nb);
+        else
+            sweep_t<false>(a, s, r0, nrows, k0, bp, k1, nb);
+    } else {
+        if (a.vec_ok)
+            sweep_tc<true, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, k1, nb);
+        else
+            sweep_tc<false, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, k1, nb);
+    }
+}
+
+template <int PREC>
 __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // persistent: L, gamma, W, Bf, W'; tile buffers; the factor's temporaries G, beta, B
@@ -374,6 +665,17 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     s.G = reinterpret_cast<double*>(s.Xs);
     s.beta = s.G + kPB * kPB;
     s.Bm = s.beta + kPB * kPB;
+    {
+        unsigned short* h = reinterpret_cast<unsigned short*>(s.flag + 4);
+        s.Uh = h; h += kPB * HP;
+        s.Ul = h; h += kPB * HP;
+        s.Wh = h; h += CT * WPT;
+        s.Wl = h; h += CT * WPT;
+        s.Xh = h; h += CT * HP;
+        s.Xl = h; h += CT * HP;
+        s.Vh = h; h += kPB * HP;
+        s.Vl = h;
+    }
     static_assert(3 * kPB * kPB * sizeof(double) <= 2 * CT * XLD * sizeof(float), "factor temporaries fit the tiles");
 
     const int N = a.nens, b = a.panel_b;
@@ -402,7 +704,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     __syncthreads();
     // ---- dots of panel 0 with every column
     int nb = b < N ? b : N;
-    sweep(a, s, r0, nrows, 0, 0, 0, nb);
+    sweep<PREC>(a, s, r0, nrows, 0, 0, 0, nb);
     if (!reduce_panel(a, s, nb * 2 * N, epoch)) return;
 
     for (int k0 = 0; k0 < N; k0 += b) {
@@ -443,7 +745,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
         }
         nb = (N - k1) < b ? (N - k1) : b;
         // every CTA has read coefg; it is rewritten only after the next barrier
-        sweep(a, s, r0, nrows, k0, bp, k1, nb);
+        sweep<PREC>(a, s, r0, nrows, k0, bp, k1, nb);
         if (nb > 0) {
             if (!reduce_panel(a, s, nb * ((N - k1) + N), epoch)) return;
         } else {
@@ -452,26 +754,32 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     }
 }
 
-size_t panel_smem() {
-    return sizeof(double) * (kPB * kPB + kPB + 32) +
-           sizeof(float) * (2 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
+size_t panel_smem(int prec) {
+    const size_t base = sizeof(double) * (kPB * kPB + kPB + 32) +
+                        sizeof(float) * (2 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
+    const size_t tc = sizeof(unsigned short) * 2 * (2 * kPB * HP + CT * WPT + CT * HP);
+    return base + (prec ? tc : 0);
+}
+
+const void* panel_kernel_ptr(int prec) {
+    return prec == 1 ? (const void*)ism_panel_kernel<1>
+                     : prec == 2 ? (const void*)ism_panel_kernel<2> : (const void*)ism_panel_kernel<0>;
 }
 
 }  // namespace
 
 int panel_max_b() { return kPB; }
 
-cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, PanelLaunch* L) {
+cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, PanelLaunch* L) {
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const size_t smem = panel_smem();
-    if ((e = cudaFuncSetAttribute(ism_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    const size_t smem = panel_smem(prec);
+    const void* fn = panel_kernel_ptr(prec);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ism_panel_kernel, kPT, smem)) != cudaSuccess)
-        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPT, smem)) != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     occ = occ > 2 ? 2 : occ;
     int64_t grid = (int64_t)nsm * occ;
@@ -485,6 +793,7 @@ cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, PanelLaunch* L) {
     L->smem = smem;
     L->rows_per_blk = (int)rpb;
     L->b = b;
+    L->prec = prec;
     L->part_stride = (int64_t)b * 2 * nens;   // largest nb * ncols
     return cudaSuccess;
 }
@@ -494,9 +803,10 @@ cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s) {
     a.panel_b = L.b;
     a.part_stride = L.part_stride;
     void* args[] = {&a};
-    cudaError_t e = cudaFuncSetAttribute(ism_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    const void* fn = panel_kernel_ptr(L.prec);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void*)ism_panel_kernel, dim3(L.grid), dim3(L.threads), args, L.smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(L.grid), dim3(L.threads), args, L.smem, s);
 }
 
 }  // namespace enkf

@@ -1,0 +1,115 @@
+"""Parity of the tensor-core panel forms with the FP64 oracle.
+
+ENKF_PANEL_BF16 runs the trailing update and the dots on tensor cores with split
+BF16 operands (x = hi + lo, three products; each operand kept to ~2^-17);
+ENKF_PANEL_FP16 uses one FP16 product (unit roundoff 2^-11).  Both store in FP32,
+accumulate in FP32 and form the level denominators in FP64.  Tolerances WITHOUT
+refinement, stated per result (relative Frobenius error against the oracle on the
+same FP32 inputs; M = V^T Z carries the conditioning of R + V V^T, hence the
+gamma factor):
+
+    mode          Z       X_A      M
+    PANEL_BF16    1e-4    5e-5     2e-5 * max(1, gamma_max/10)
+    PANEL_FP16    5e-3    1e-3     2e-3 * max(1, gamma_max/10)
+
+The measured errors are printed so the tables in the design notes can quote them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.util import host, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1302_3876_gb300 import enkf  # noqa: E402
+
+BARS = {
+    enkf.ENKF_PANEL_BF16: {"Z": 1e-4, "XA": 5e-5, "M": 2e-5},
+    enkf.ENKF_PANEL_FP16: {"Z": 5e-3, "XA": 1e-3, "M": 2e-3},
+}
+NAME = {enkf.ENKF_PANEL_BF16: "PANEL_BF16", enkf.ENKF_PANEL_FP16: "PANEL_FP16"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    enkf.load(build_if_missing=True)
+
+
+def problem(seed, nobs, nens, nstate):
+    s = synth.uniform(seed, 1, nstate, 0.5, 2.0)
+    dXB = synth.normal_matrix(seed, 2, nstate, nens, row_scale=s).astype(np.float32).astype(np.float64)
+    r = synth.uniform(seed, 3, nobs, 0.5, 1.5).astype(np.float32).astype(np.float64)
+    D = synth.normal_matrix(seed, 4, nobs, nens).astype(np.float32).astype(np.float64)
+    V = oracle.observe_deviations(dXB, nobs, max(1, nstate // nobs)).astype(np.float32).astype(np.float64)
+    return r, V, D, dXB
+
+
+def run(mode, r, V, D, dXB, panel_b=0):
+    nens, nobs = V.shape
+    nstate = dXB.shape[1]
+    plan = enkf.Plan(nstate, nobs, nens, mode, panel_b=panel_b)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    tr, tV, tD, tdX = t(r), t(V), t(D), t(dXB)
+    tXA = torch.empty_like(tdX)
+    tZ = torch.empty_like(tD)
+    tM = torch.empty(nens * nens, device="cuda")
+    inf = plan.analysis(tr, tV, tD, dXB=tdX, XB=tdX, XA=tXA, Z=tZ, M=tM, info=True)
+    assert inf.status == 0
+    out = {"Z": host(tZ), "XA": host(tXA), "M": host(tM).reshape(nens, nens).T, "info": inf}
+    plan.close()
+    return out
+
+
+def check(mode, dev, r, V, D, dXB, label):
+    Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
+    M = oracle.vtz(V, Z)
+    XA = oracle.analysis_update(dXB, dXB, M)
+    errs = {"Z": rel(dev["Z"], Z), "XA": rel(dev["XA"], XA), "M": rel(dev["M"], M),
+            "increment": rel(dev["XA"] - dXB, XA - dXB)}
+    print(f"{NAME[mode]} {label}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()) +
+          f", gamma_max {gamma.max():.1f}")
+    bar = BARS[mode]
+    assert errs["Z"] <= bar["Z"], errs
+    assert errs["XA"] <= bar["XA"], errs
+    assert errs["M"] <= bar["M"] * max(1.0, gamma.max() / 10.0), errs
+    assert dev["info"].gamma_max == pytest.approx(gamma.max(), rel=1e-4)
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16])
+@pytest.mark.parametrize("nobs,nens,panel_b", [(1, 4, 0), (31, 5, 0), (129, 16, 8), (4099, 64, 32), (20000, 48, 16),
+                                               (20011, 128, 32), (9000, 256, 32), (5000, 37, 5)])
+def test_tensor_core_panel_random(mode, nobs, nens, panel_b):
+    nstate = 3 * nobs + 1
+    r, V, D, dXB = problem(9000 + nobs + nens, nobs, nens, nstate)
+    dev = run(mode, r, V, D, dXB, panel_b)
+    check(mode, dev, r, V, D, dXB, f"nobs={nobs} nens={nens} b={panel_b}")
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16])
+def test_large_single_full_size(mode):
+    w = synth.large_single(dtype=np.float32)
+    dXB = w["dXB"].astype(np.float64)
+    r = w["r"].astype(np.float64)
+    D = w["D"].astype(np.float64)
+    V = oracle.observe_deviations(dXB, w["nobs"], 4).astype(np.float32).astype(np.float64)
+    dev = run(mode, r, V, D, dXB)
+    check(mode, dev, r, V, D, dXB, "large_single full size")
+
+
+def test_panel_single_full_size():
+    """Nobs = 2^20, Nens = 256, Nstate = 2^22 (the panel workload), split-BF16 tensor cores."""
+    w = synth.panel_single()
+    dXB = w["dXB"].astype(np.float64)
+    r = w["r"].astype(np.float64)
+    D = w["D"].astype(np.float64)
+    del w
+    V = oracle.observe_deviations(dXB, 1 << 20, 4).astype(np.float32).astype(np.float64)
+    dev = run(enkf.ENKF_PANEL_BF16, r, V, D, dXB)
+    check(enkf.ENKF_PANEL_BF16, dev, r, V, D, dXB, "panel_single full size")
