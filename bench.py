@@ -157,6 +157,20 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def aggregate_ranks(t_ms: float, steps: int, world: int, device=None):
+    """Replicas on `world` ranks each time `steps` analyses: the job's time is the
+    slowest rank's (all-reduce MAX), and the whole-job throughput counts every
+    rank's analyses: value = world * steps / t_max."""
+    t_max = t_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, world * steps / (t_max / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,7 +272,8 @@ def run_ours(args):
     M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
     mode = {"panel32": enkf.ENKF_PANEL_FP32, "bf16": enkf.ENKF_PANEL_BF16, "fp16": enkf.ENKF_PANEL_FP16,
             "fp32": enkf.ENKF_FP32}[args.mode]
-    plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode != "fp32" else 0, device=dev)
+    plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode != "fp32" else 0,
+                     flags=enkf.ENKF_FLAG_REFINE if args.refine else 0, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -282,12 +297,7 @@ def run_ours(args):
     t_ms = ev0.elapsed_time(ev1)
     phases = enkf.enkf_ism_profile_read(plan.handle)
     enkf.enkf_ism_profile(plan.handle, False)
-    t_max = t_ms
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max, value = aggregate_ranks(t_ms, args.steps, world, dev)
 
     # end to end through the API with host buffers: H2D of the inputs, the analysis, D2H of X_A
     h_XA = torch.empty(XA.shape, dtype=XA.dtype).pin_memory()
@@ -404,6 +414,7 @@ def run_ours(args):
                             "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)" % args.panel_b,
                             "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)" % args.panel_b,
                             "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}[args.mode],
+                   "refine": bool(args.refine),
                    "l2": "inputs 1.3 GB > L2; no flush", "parallelism": f"replicas x{world}"},
         "gflops": flops(NSTATE, NOBS, NENS) / (ms_step / 1e3) / 1e9,
         "gamma_min": inf.gamma_min, "gamma_max": inf.gamma_max,
@@ -421,6 +432,180 @@ def run_ours(args):
     plan.close()
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (not the default line): the panel workload, the batched
+# workload and the Lorenz-96 cycle with the learned surrogate.
+# ---------------------------------------------------------------------------
+
+def _events_ms(fn, k):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(k):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def run_panel_single(args):
+    """Nstate = 2^22, Nobs = 2^20 (every 4th), Nens = 256: the tensor-core panel forms (split BF16 and
+    FP16, each with one refinement step), the FP32-core panel form, and the plain FP64 path."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+    nstate, nobs, nens = 1 << 22, 1 << 20, 256
+    w = synth.panel_single(dtype=np.float32)
+    dev = torch.device("cuda")
+    dX = torch.from_numpy(w["dXB"]).to(dev)
+    D = torch.from_numpy(w["D"]).to(dev)
+    r = torch.from_numpy(w["r"]).to(dev)
+    del w
+    V = torch.empty(nens, nobs, device=dev)
+    XA = torch.empty_like(dX)
+    Mo = torch.empty(nens * nens, device=dev)
+    results = {}
+    outs = {}
+    for name, mode, flags in (("bf16+refine", enkf.ENKF_PANEL_BF16, enkf.ENKF_FLAG_REFINE),
+                              ("fp16+refine", enkf.ENKF_PANEL_FP16, enkf.ENKF_FLAG_REFINE),
+                              ("bf16", enkf.ENKF_PANEL_BF16, 0), ("panel32", enkf.ENKF_PANEL_FP32, 0)):
+        plan = enkf.Plan(nstate, nobs, nens, mode, flags=flags, device=dev)
+
+        def step():
+            plan.obs_prep(4, 0, None, dX, V)
+            plan.analysis(r, V, D, dXB=dX, XB=dX, XA=XA, M=Mo)
+
+        for _ in range(args.warmup):
+            step()
+        enkf.enkf_ism_profile(plan.handle, True)
+        ms = _events_ms(step, args.steps)
+        ph = enkf.enkf_ism_profile_read(plan.handle)
+        results[name] = {"ms_per_step": ms, "analyses_per_s": 1e3 / ms,
+                         "phases_ms": {k: v[0] / max(v[1], 1) for k, v in ph.items()}}
+        outs[name] = (XA.clone(), Mo.clone())
+        plan.close()
+    ref64 = None
+    if not args.no_fp64:
+        dX64, D64, r64 = dX.double(), D.double(), r.double()
+        V64 = torch.empty(nens, nobs, dtype=torch.float64, device=dev)
+        XA64 = torch.empty_like(dX64)
+        M64 = torch.empty(nens * nens, dtype=torch.float64, device=dev)
+        plan = enkf.Plan(nstate, nobs, nens, enkf.ENKF_FP64, device=dev)
+
+        def step64():
+            plan.obs_prep(4, 0, None, dX64, V64)
+            plan.analysis(r64, V64, D64, dXB=dX64, XB=dX64, XA=XA64, M=M64)
+
+        step64()
+        ms64 = _events_ms(step64, 1)
+        results["fp64_plain"] = {"ms_per_step": ms64, "analyses_per_s": 1e3 / ms64}
+        for name, (xa, mo) in outs.items():
+            results[name]["rel_err_vs_fp64"] = {
+                "XA": float(torch.linalg.norm(xa.double() - XA64) / torch.linalg.norm(XA64)),
+                "increment": float(torch.linalg.norm(xa.double() - XA64) / torch.linalg.norm(XA64 - dX64)),
+                "M": float(torch.linalg.norm(mo.double() - M64) / torch.linalg.norm(M64))}
+            results[name]["speedup_over_fp64_plain"] = ms64 / results[name]["ms_per_step"]
+        plan.close()
+        ref64 = ms64
+    best = min((v["ms_per_step"], k) for k, v in results.items() if k != "fp64_plain"
+               and v.get("rel_err_vs_fp64", {"XA": 0})["XA"] <= 1e-5)
+    print(json.dumps({"metric": METRIC, "workload": f"panel_single Nstate={nstate} Nobs={nobs} Nens={nens}",
+                      "value": 1e3 / best[0], "unit": METRIC, "best_path_at_1e-5": best[1],
+                      "fp64_plain_ms": ref64, "paths": results, "data": "synthetic"}), flush=True)
+
+
+def run_batch_local(args):
+    """8192 independent problems (Nobs log-uniform in [16, 4096], Nens in {32,64,96,128}) in one persistent
+    launch replayed from a CUDA graph, panel widths autotuned; plain FP64 path per problem on a sample."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+    base, descs, nout = synth.batch_local_packed(8192)
+    dev = torch.device("cuda")
+    tin = torch.from_numpy(base).to(dev)
+    tout = torch.empty(nout, device=dev)
+    plan, wsb = enkf.enkf_ism_batch_plan(descs)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    widths = enkf.enkf_ism_batch_autotune(plan, tin, tout, ws)
+    for _ in range(args.warmup):
+        enkf.enkf_ism_batch(plan, tin, tout, ws)
+    ms = _events_ms(lambda: enkf.enkf_ism_batch(plan, tin, tout, ws), args.steps)
+    enkf.enkf_ism_batch_plan_destroy(plan)
+    flops = sum(6 * d["nobs"] * d["nens"] ** 2 + 3 * d["nobs"] * d["nens"] + 2 * d["nobs"] * d["nens"] ** 2
+                for d in descs)
+    # plain FP64 comparator on every 32nd problem, scaled by 32
+    sample = descs[::32]
+    t64 = 0.0
+    for d in sample:
+        n, N = d["nobs"], d["nens"]
+        V = tin[d["V"]:d["V"] + n * N].view(N, n).double()
+        Dm = tin[d["D"]:d["D"] + n * N].view(N, n).double()
+        rr = tin[d["r"]:d["r"] + n].double()
+        Z = torch.empty_like(Dm)
+        Mm = torch.empty(N * N, dtype=torch.float64, device=dev)
+        p = enkf.Plan(1, n, N, enkf.ENKF_FP64, device=dev)
+        p.analysis(rr, V, Dm, Z=Z, M=Mm)
+        t64 += _events_ms(lambda: p.analysis(rr, V, Dm, Z=Z, M=Mm), 1)
+        p.close()
+    ms64 = t64 * len(descs) / len(sample)
+    print(json.dumps({"metric": "problems/s", "workload": "batch_local 8192 problems", "value": 8192 / (ms / 1e3),
+                      "unit": "problems/s", "ms_per_batch": ms, "gflops": flops / (ms / 1e3) / 1e9,
+                      "fp32_alu_frac": flops / (ms / 1e3) / 1e12 / fp32_alu_peak_tflops(),
+                      "widths_per_class": widths,
+                      "fp64_plain_per_problem_ms_est": ms64,
+                      "speedup_over_fp64_plain": ms64 / ms, "data": "synthetic"}), flush=True)
+
+
+def run_lorenz_cycle(args):
+    """Lorenz-96 Nstate=4096, Nens=256, 200 cycles of 5 RK4 steps, every 2nd variable observed, R = 0.25 I:
+    the filter with RK4, with the learned surrogate (trained on filter trajectories of a separate seed), and
+    with persistence."""
+    import torch
+    from paper_1302_3876_gb300 import cycle as C
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+    t0 = time.perf_counter()
+    train = C.LorenzCycle(4096, 256, seed=555)
+    pairs = []
+    train.run(args.train_cycles, "rk4", collect=pairs)
+    xs = torch.cat([a for a, _ in pairs]).contiguous()
+    ys = torch.cat([b for _, b in pairs]).contiguous()
+    train.close()
+    del pairs
+    ts = time.perf_counter()
+    master, packed, log = C.train_surrogate(xs, ys, steps=args.train_steps, batch=16, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - ts
+    out = {}
+    for method in ("rk4", "surrogate", "persistence"):
+        cyc = C.LorenzCycle(4096, 256)
+        if method == "surrogate":
+            cyc.set_surrogate(packed)
+        rmse, cps, _ = cyc.run(200, method)
+        out[method] = {"analysis_rmse": rmse, "cycles_per_s": cps}
+        cyc.close()
+    # forecast-only timing of the two models on the same ensemble
+    cyc = C.LorenzCycle(4096, 256)
+    cyc.set_surrogate(packed)
+    X = cyc.X
+    rk = _events_ms(lambda: enkf.enkf_forecast(X, 8.0, 0.01, 5), 20)
+    sg = _events_ms(lambda: enkf.enkf_forecast(X, 8.0, 0.01, 1, method=enkf.ENKF_FORECAST_SURROGATE,
+                                               weights=packed, workspace=cyc.sur_ws), 20)
+    cyc.close()
+    print(json.dumps({"metric": "cycles/s", "workload": "lorenz_cycle Nstate=4096 Nens=256, 200 cycles",
+                      "value": out["surrogate"]["cycles_per_s"], "unit": "cycles/s", "methods": out,
+                      "forecast_ms": {"rk4_5_steps": rk, "surrogate": sg,
+                                      "surrogate_tflops": 2 * 4096 * 256 * 41600 / (sg / 1e3) / 1e12},
+                      "training": {"pairs": int(xs.shape[0]), "steps": args.train_steps, "seconds": train_s,
+                                   "mse_log": log[-3:]},
+                      "wall_s": time.perf_counter() - t0, "data": "synthetic"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,11 +620,22 @@ def main():
                     help="headline path: panel form on FP32 CUDA cores (panel32), on tensor cores with split BF16 "
                          "(bf16) or FP16 (fp16) operands, or the FP32 level-streaming path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
+    ap.add_argument("--refine", action="store_true", help="one step of iterative refinement (panel modes)")
+    ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle"],
+                    default="large_single")
+    ap.add_argument("--train-cycles", type=int, default=60)
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--scale-div", type=int, default=1,
                     help="divide Nobs and Nstate by this factor (small case for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "panel_single":
+        run_panel_single(args)
+    elif args.workload == "batch_local":
+        run_batch_local(args)
+    elif args.workload == "lorenz_cycle":
+        run_lorenz_cycle(args)
     else:
         run_ours(args)
 

@@ -77,7 +77,14 @@ typedef enum {
 } enkf_mode;
 
 /* Plan flags. */
-#define ENKF_FLAG_REFINE        0x1u  /* panel modes: one iterative-refinement sweep of Z */
+#define ENKF_FLAG_REFINE        0x1u  /* panel modes: one step of iterative refinement of Z and M:
+                                         the residual R^{-1}(D - (R + V V^T) Z) with V^T Z and the
+                                         N-term sums formed from exact products and compensated sums,
+                                         corrected by the stored factors (final U columns, gamma and L
+                                         from one Gram V^T U); M = V^T (Z + delta) / sqrt(Nens - 1).
+                                         One step contracts the error by about u * gamma_max (u the
+                                         operand precision): effective for PANEL_FP32 and PANEL_BF16,
+                                         not for PANEL_FP16 once gamma_max approaches 1/u = 2^11 */
 #define ENKF_FLAG_NO_CHECKS     0x2u  /* skip the device-side gamma / finiteness checks */
 #define ENKF_FLAG_TEST_TIMEOUT  0x4u  /* test only: one CTA skips its first grid-barrier arrival,
                                          so the others' bounded wait expires (ENKF_ERR_TIMEOUT) */
@@ -285,7 +292,7 @@ ENKF_API enkf_status enkf_surrogate_train_step(float* master, float* adam_m, flo
  * the elapsed milliseconds of each phase into ms[phase] and the number of
  * launches into count[phase] (arrays of ENKF_PROFILE_PHASES, caller-owned host
  * memory), and clears the record.  Phases: 0 obs prep, 1 level streaming (Step 1
- * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update.
+ * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update, 5 refinement.
  */
 #define ENKF_PROFILE_PHASES 8
 ENKF_API enkf_status enkf_ism_profile(enkf_ism_plan_t plan, int32_t enable);

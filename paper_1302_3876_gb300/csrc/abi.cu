@@ -55,7 +55,8 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        total;
+        off_delta, off_P, off_Md, total;
+    bool refine;
     // latched status of the previous call
     int* h_status;            // pinned host word
     cudaEvent_t done;
@@ -161,6 +162,12 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_M = o; o = align256(o + p->w * N * N);
     p->off_M64 = o; o = align256(o + sizeof(double) * N * N);
     p->off_Msplit = o; o = align256(o + 2 * sizeof(uint16_t) * N * (size_t)xa_tc_kpad(nens));
+    p->refine = panel && (flags & ENKF_FLAG_REFINE);
+    if (p->refine) {
+        p->off_delta = o; o = align256(o + sizeof(float) * (size_t)p->ldzw * N);
+        p->off_P = o; o = align256(o + sizeof(double) * N * N);
+        p->off_Md = o; o = align256(o + sizeof(double) * N * N);
+    }
     p->total = o;
     e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
@@ -312,6 +319,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     a.test_skip_arrival = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 1 : 0;
     a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
     int slot = prof_begin(p, 1, s);
+    PanelArgs panel_args;
     if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16) {
         PanelArgs pa;
         pa.nobs = p->nobs;
@@ -337,22 +345,58 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.vec_ok = (((uintptr_t)a.U | (uintptr_t)a.Z | (uintptr_t)V) % 16 == 0) && (a.ldu % 4 == 0) &&
                     (a.ldz % 4 == 0) && (ldv % 4 == 0) && (p->P.rows_per_blk % 4 == 0);
         pa.timeout_ns = a.timeout_ns;
+        pa.refine = 0;
+        pa.Qg = nullptr;
         CU(panel_launch(p->P, pa, s), "panel launch");
+        panel_args = pa;
     } else {
         CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
     }
     prof_end(p, slot, s);
 
-    if (M || dXB) {
+    if (M || dXB || p->refine) {
         double* Q = (double*)(ws + p->off_Q);
-        slot = prof_begin(p, 2, s);
-        CU(gram_upper(p->fp64, p->nobs, p->nens, V, ldv, a.U, p->ldu, (double*)(ws + p->off_Qpart), p->nsplit, Q, s),
-           "gram launch");
-        prof_end(p, slot, s);
         void* Mp = M ? M : (void*)(ws + p->off_M);
-        slot = prof_begin(p, 3, s);
-        CU(assemble_M(p->fp64, p->nens, Q, a.C, a.gamma, Mp, (double*)(ws + p->off_M64), s), "assemble_M launch");
-        prof_end(p, slot, s);
+        double* M64 = (double*)(ws + p->off_M64);
+        if (!p->refine) {
+            slot = prof_begin(p, 2, s);
+            CU(gram_upper(p->fp64, p->nobs, p->nens, V, ldv, a.U, p->ldu, (double*)(ws + p->off_Qpart), p->nsplit, Q,
+                          s),
+               "gram launch");
+            prof_end(p, slot, s);
+            slot = prof_begin(p, 3, s);
+            CU(assemble_M(p->fp64, p->nens, Q, a.C, a.gamma, Mp, M64, s), "assemble_M launch");
+            prof_end(p, slot, s);
+        } else {
+            // One step of iterative refinement: P = V^T Z (compensated Gram), the scaled residual
+            // R^-1 (D - r o Z - V P), the stored factors (final U columns, gamma' and L from
+            // one Gram Q = V^T U) applied to it giving delta, then Z += delta and
+            // M = (P + V^T delta) / sqrt(N - 1).
+            slot = prof_begin(p, 5, s);
+            double* P = (double*)(ws + p->off_P);
+            double* Pd = (double*)(ws + p->off_Md);
+            double* part = (double*)(ws + p->off_Qpart);
+            float* delta = (float*)(ws + p->off_delta);
+            CU(gram_comp(p->nobs, p->nens, (const float*)V, ldv, (const float*)Zp, ldzp, part, p->nsplit, P, s),
+               "refine Gram V^T Z");
+            CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
+                               (const float*)Zp, ldzp, P, delta, p->ldzw, s),
+               "refine residual");
+            CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, s), "refine Gram V^T U");
+            PanelArgs ra = panel_args;
+            ra.Qg = Q;
+            ra.refine = 1;
+            ra.Z = delta;
+            ra.ldz = p->ldzw;
+            ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
+            CU(cudaMemsetAsync(&ctl->barrier, 0, sizeof(unsigned), s), "barrier reset");
+            CU(panel_launch(p->P, ra, s), "stored-factor correction");
+            CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, s),
+               "refine Gram V^T delta");
+            CU(refine_apply(p->nobs, p->nens, (float*)Zp, ldzp, delta, p->ldzw, P, Pd, M64, (float*)Mp, s),
+               "refine apply");
+            prof_end(p, slot, s);
+        }
         if (dXB) {
             slot = prof_begin(p, 4, s);
             if (p->fp64)

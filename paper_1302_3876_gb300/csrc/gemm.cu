@@ -29,17 +29,23 @@ constexpr int GR = 32;   // rows per smem stage
 template <typename T>
 __global__ void __launch_bounds__(256) gram_upper_kernel(int64_t nrows, int n, const T* __restrict__ A, int64_t lda,
                                                          const T* __restrict__ B, int64_t ldb, int64_t rows_per_split,
-                                                         double* __restrict__ Qpart) {
+                                                         double* __restrict__ Qpart, int full) {
     __shared__ T As[GT][GR + 1];
     __shared__ T Bs[GT][GR + 1];
-    // map blockIdx.x to an upper tile (kb <= mb)
+    // map blockIdx.x to a tile: every (kb, mb) when full, else the upper tiles (kb <= mb)
     const int nt = (n + GT - 1) / GT;
-    int t = blockIdx.x, kb = 0;
-    while (t >= nt - kb) {
-        t -= nt - kb;
-        ++kb;
+    int kb = 0, mb = 0;
+    if (full) {
+        kb = blockIdx.x / nt;
+        mb = blockIdx.x % nt;
+    } else {
+        int t = blockIdx.x;
+        while (t >= nt - kb) {
+            t -= nt - kb;
+            ++kb;
+        }
+        mb = kb + t;
     }
-    const int mb = kb + t;
     const int split = blockIdx.y;
     const int64_t j0 = (int64_t)split * rows_per_split;
     const int64_t j1 = min(j0 + rows_per_split, nrows);
@@ -90,17 +96,18 @@ __global__ void __launch_bounds__(256) gram_upper_kernel(int64_t nrows, int n, c
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int m = mb * GT + tx * 4 + q;
-            if (k < n && m < n && k < m) out[(int64_t)k * n + m] = accd[i][q] + (double)acc[i][q];
+            if (k < n && m < n && (full || k < m)) out[(int64_t)k * n + m] = accd[i][q] + (double)acc[i][q];
         }
     }
 }
 
-__global__ void gram_reduce_kernel(int n, int nsplit, const double* __restrict__ Qpart, double* __restrict__ Q) {
+__global__ void gram_reduce_kernel(int n, int nsplit, const double* __restrict__ Qpart, double* __restrict__ Q,
+                                   int full) {
     const int64_t nn = (int64_t)n * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(e / n), m = (int)(e % n);
         double s = 0.0;
-        if (k < m)
+        if (full || k < m)
             for (int p = 0; p < nsplit; ++p) s += Qpart[(int64_t)p * nn + e];
         Q[e] = s;
     }
@@ -347,22 +354,34 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
     return (int32_t)s;
 }
 
-cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
-                       double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
+static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
+                               int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
     const int nt = (n + GT - 1) / GT;
-    const int tiles = nt * (nt + 1) / 2;
+    const int tiles = full ? nt * nt : nt * (nt + 1) / 2;
     int64_t rps = (nrows + nsplit - 1) / nsplit;
     rps = (rps + GR - 1) / GR * GR;
     dim3 grid(tiles, nsplit);
     if (fp64)
-        gram_upper_kernel<double><<<grid, 256, 0, s>>>(nrows, n, (const double*)A, lda, (const double*)B, ldb, rps, Qpart);
+        gram_upper_kernel<double><<<grid, 256, 0, s>>>(nrows, n, (const double*)A, lda, (const double*)B, ldb, rps, Qpart,
+                                                       full);
     else
-        gram_upper_kernel<float><<<grid, 256, 0, s>>>(nrows, n, (const float*)A, lda, (const float*)B, ldb, rps, Qpart);
+        gram_upper_kernel<float><<<grid, 256, 0, s>>>(nrows, n, (const float*)A, lda, (const float*)B, ldb, rps, Qpart,
+                                                      full);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
-    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, nsplit, Qpart, Q);
+    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, nsplit, Qpart, Q, full);
     return cudaGetLastError();
+}
+
+cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
+    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 0, s);
+}
+
+cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                      double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
+    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 1, s);
 }
 
 cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C, const double* gamma, void* M,

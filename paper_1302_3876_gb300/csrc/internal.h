@@ -66,6 +66,8 @@ struct PanelArgs {
     int32_t panel_b;
     int32_t check;
     int32_t vec_ok;                // 16-byte aligned columns (U, Z, V) and row blocks
+    int32_t refine;                // 1: stored-factor recurrence on the columns in Z (R^-1 times a residual)
+    const double* Qg;              // [nens][nens] Gram V^T U of the final U columns (refinement)
     uint64_t timeout_ns;
 };
 
@@ -88,6 +90,25 @@ cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
 cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
                        int64_t ldb, double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
 int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
+// Full Gram P[k][m] = sum_j A[j,k] B[j,m] (every k, m), same splitting and fixed-order reduction.
+cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
+                      double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
+
+// Refinement helpers (FP32 storage):
+//   gram_comp:       P[k][m] = sum_j A[j,k] B[j,m] (every k, m; row-major) with exact
+//                    products and compensated sums folded into FP64 (same splitting and
+//                    fixed-order reduction as gram_full; part holds nsplit * n * n doubles);
+//   refine_residual: delta = (D - r o Z - V P) / r with P = V^T Z (row-major P[m][i]),
+//                    the N-term sums with exact products and compensated FP32 sums;
+//   refine_apply:    Z += delta and M = (P + Pd) / sqrt(n - 1) (column-major M[k + i n],
+//                    written to M64 and/or M when not NULL).
+cudaError_t gram_comp(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
+                      double* part, int32_t nsplit, double* P, cudaStream_t s);
+cudaError_t refine_residual(int64_t nobs, int32_t n, const float* r, const float* V, int64_t ldv, const float* D,
+                            int64_t ldd, const float* Z, int64_t ldz, const double* P, float* delta, int64_t ldo,
+                            cudaStream_t s);
+cudaError_t refine_apply(int64_t nobs, int32_t n, float* Z, int64_t ldz, const float* delta, int64_t ldd,
+                         const double* P, const double* Pd, double* M64, float* M, cudaStream_t s);
 
 // M = (I - triu(Q,1)) diag(1/gamma) C / sqrt(nens - 1)  (nens x nens, column-major
 // output in T: M[m + e*nens]).  C is [level][column].

@@ -191,11 +191,12 @@ __device__ __forceinline__ void stage_cols(float* dst, int ld, int ncols_tile, i
 // Thread tiles use interleaved columns (c = x + 16 q) so that the 16-byte shared
 // loads of 16 lanes fall in distinct banks.
 template <bool VEC>
-__device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
-                        int nb) {
+__device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
+                        int kv, int nb, int aoff, bool materialize) {
     const int N = a.nens;
+    const int k1 = ku;   // trailing U columns start here (N: none)
     const int ncols = (N - k1) + N;
-    const int ncols_prev = ncols + bp;
+    const int ncols_prev = ncols + aoff;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float* V = static_cast<const float*>(a.V);
     const int ntiles = (int)((nrows + RT - 1) / RT);
@@ -209,7 +210,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
             float* As = s.VNs + 2 * kPB * RT;    // [kPB][CT] scratch after the double-buffered tiles
             for (int e = tid; e < bp * CT; e += kPT) {
                 const int u = e >> 6, c = e & 63;
-                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]) : 0.f;
+                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + aoff]) : 0.f;
             }
             __syncthreads();
             for (int e = tid; e < bp * CT; e += kPT) {
@@ -226,7 +227,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
             for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
         auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
-        auto vcol = [&](int t) { return V + (int64_t)(k1 + t) * a.ldv; };
+        auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
@@ -337,7 +338,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
         }
     }
     // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
-    if (bp > 0) {
+    if (bp > 0 && materialize) {
         for (int64_t rr = 0; rr < nrows; rr += RT) {
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
@@ -423,12 +424,13 @@ __device__ __forceinline__ void put4(unsigned short* h, unsigned short* l, float
 }
 
 template <bool VEC, int PREC>
-__device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
-                         int nb) {
+__device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
+                         int kv, int nb, int aoff, bool materialize) {
     constexpr bool SPLIT = Tc<PREC>::split;
     const int N = a.nens;
+    const int k1 = ku;
     const int ncols = (N - k1) + N;
-    const int ncols_prev = ncols + bp;
+    const int ncols_prev = ncols + aoff;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float* V = static_cast<const float*>(a.V);
     const int ntiles = (int)((nrows + RT - 1) / RT);
@@ -440,7 +442,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
             float* As = s.VNs + 2 * kPB * RT;    // [kPB][CT]
             for (int e = tid; e < bp * CT; e += kPT) {
                 const int u = e >> 6, c = e & 63;
-                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + bp]) : 0.f;
+                As[u * CT + c] = c < ncl ? (float)__ldcg(&a.coefg[u * ncols_prev + c0 + c + aoff]) : 0.f;
             }
             __syncthreads();
             // W'[t][c] into [col][t] 16-bit tiles; t >= bp is zero padding of K
@@ -461,7 +463,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
             for (int h = 0; h < 4; ++h) acc2[mt][h] = 0.f;
         auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
-        auto vcol = [&](int t) { return V + (int64_t)(k1 + t) * a.ldv; };
+        auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
@@ -610,7 +612,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
         }
     }
     // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
-    if (bp > 0) {
+    if (bp > 0 && materialize) {
         for (int64_t rr = 0; rr < nrows; rr += RT) {
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
@@ -630,19 +632,69 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
     }
 }
 
+// Sweep over this CTA's rows: update the trailing columns (u_ku.., all z) with the
+// panel [k0, k0+bp) and accumulate the dots with v_kv.. (nb of them).  aoff: offset
+// of the trailing columns in the previous sweep's column list; materialize: write
+// the panel's final U columns.
 template <int PREC>
-__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int k1,
-                      int nb) {
+__device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
+                      int kv, int nb, int aoff, bool materialize) {
     if (PREC == 0) {
         if (a.vec_ok)
-            sweep_t<true>(a, s, r0, nrows, k0, bp, k1, nb);
+            sweep_t<true>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
         else
-            sweep_t<false>(a, s, r0, nrows, k0, bp, k1, nb);
+            sweep_t<false>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
     } else {
         if (a.vec_ok)
-            sweep_tc<true, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, k1, nb);
+            sweep_tc<true, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
         else
-            sweep_tc<false, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, k1, nb);
+            sweep_tc<false, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
+    }
+}
+
+// Stored-factor recurrence for the refinement (FP32 CUDA-core sweeps): applies
+//   x <- x - h_m (v_m^T x),  h_m = u_m / gamma'_m,  gamma'_m = 1 + v_m^T u_m,   m = 0..N-1
+// to the N columns held in Z (R^-1 times a residual), where u_m are the final U columns
+// left by the solve and every inner product v_k^T u_m comes from one Gram Q = V^T U
+// (row-major), so the b x b factors need no reduction.  Per panel: c = (I + L)^{-1}
+// V_P^T x with L[m][l] = Q[m][l] / gamma'_l (l < m), then x <- x - U_P diag(1/gamma') c.
+__device__ void refine_body(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, unsigned& epoch) {
+    const int N = a.nens, b = a.panel_b;
+    const int tid = threadIdx.x;
+    int nb = b < N ? b : N;
+    sweep<0>(a, s, r0, nrows, 0, 0, N, 0, nb, 0, false);
+    if (!reduce_panel(a, s, nb * N, epoch)) return;
+    for (int k0 = 0; k0 < N; k0 += b) {
+        const int bp = (N - k0) < b ? (N - k0) : b;
+        const int k1 = k0 + bp;
+        if (tid < 32) {
+            // gamma' and L of this panel from the Gram, then W = diag(1/gamma') (I + L)^{-1}
+            for (int m = tid; m < bp; m += 32) s.gam[m] = 1.0 + a.Qg[(int64_t)(k0 + m) * N + (k0 + m)];
+            __syncwarp();
+            for (int e = tid; e < bp * bp; e += 32) {
+                const int m = e / bp, l = e % bp;
+                s.L[m * kPB + l] = (l < m) ? a.Qg[(int64_t)(k0 + m) * N + (k0 + l)] / s.gam[l] : 0.0;
+            }
+            __syncwarp();
+            const int q = tid;
+            if (q < bp) {
+                float tcol[kPB];
+                for (int m = 0; m < bp; ++m) {
+                    float v = (m == q) ? 1.f : 0.f;
+                    for (int l = q; l < m; ++l) v = fmaf(-(float)s.L[m * kPB + l], tcol[l], v);
+                    tcol[m] = (m < q) ? 0.f : v;
+                }
+                for (int m = 0; m < bp; ++m) s.W[m * kPB + q] = (float)((double)tcol[m] / s.gam[m]);
+            }
+        }
+        __syncthreads();
+        nb = (N - k1) < b ? (N - k1) : b;
+        sweep<0>(a, s, r0, nrows, k0, bp, N, k1, nb, 0, false);
+        if (nb > 0) {
+            if (!reduce_panel(a, s, nb * N, epoch)) return;
+        } else {
+            break;
+        }
     }
 }
 
@@ -688,6 +740,10 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     const float* D = static_cast<const float*>(a.D);
     const float* r = static_cast<const float*>(a.r);
 
+    if (a.refine) {   // correction sweep: U holds the final columns, Z the scaled residual
+        refine_body(a, s, r0, nrows, epoch);
+        return;
+    }
     // ---- Step 1 (eq. SM-step-1) on this CTA's rows
     for (int c = tid / 64; c < 2 * N; c += kPT / 64) {
         const float* src = c < N ? V + (int64_t)c * a.ldv : D + (int64_t)(c - N) * a.ldd;
@@ -704,7 +760,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     __syncthreads();
     // ---- dots of panel 0 with every column
     int nb = b < N ? b : N;
-    sweep<PREC>(a, s, r0, nrows, 0, 0, 0, nb);
+    sweep<PREC>(a, s, r0, nrows, 0, 0, 0, 0, nb, 0, true);
     if (!reduce_panel(a, s, nb * 2 * N, epoch)) return;
 
     for (int k0 = 0; k0 < N; k0 += b) {
@@ -745,7 +801,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
         }
         nb = (N - k1) < b ? (N - k1) : b;
         // every CTA has read coefg; it is rewritten only after the next barrier
-        sweep<PREC>(a, s, r0, nrows, k0, bp, k1, nb);
+        sweep<PREC>(a, s, r0, nrows, k0, bp, k1, k1, nb, bp, true);
         if (nb > 0) {
             if (!reduce_panel(a, s, nb * ((N - k1) + N), epoch)) return;
         } else {

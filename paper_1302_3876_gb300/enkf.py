@@ -40,7 +40,7 @@ ENKF_FORECAST_RK4 = 0
 ENKF_FORECAST_SURROGATE = 1
 
 ENKF_PROFILE_PHASES = 8
-PROFILE_PHASE_NAMES = ("obs_prep", "ism_solve", "gram_upper", "assemble_M", "xa_update", "", "", "")
+PROFILE_PHASE_NAMES = ("obs_prep", "ism_solve", "gram_upper", "assemble_M", "xa_update", "refine", "", "")
 
 
 class EnkfError(RuntimeError):

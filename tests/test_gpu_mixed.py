@@ -51,10 +51,10 @@ def problem(seed, nobs, nens, nstate):
     return r, V, D, dXB
 
 
-def run(mode, r, V, D, dXB, panel_b=0):
+def run(mode, r, V, D, dXB, panel_b=0, flags=0):
     nens, nobs = V.shape
     nstate = dXB.shape[1]
-    plan = enkf.Plan(nstate, nobs, nens, mode, panel_b=panel_b)
+    plan = enkf.Plan(nstate, nobs, nens, mode, panel_b=panel_b, flags=flags)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
     tr, tV, tD, tdX = t(r), t(V), t(D), t(dXB)
     tXA = torch.empty_like(tdX)
@@ -65,6 +65,14 @@ def run(mode, r, V, D, dXB, panel_b=0):
     out = {"Z": host(tZ), "XA": host(tXA), "M": host(tM).reshape(nens, nens).T, "info": inf}
     plan.close()
     return out
+
+
+def errors(dev, r, V, D, dXB):
+    Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
+    M = oracle.vtz(V, Z)
+    XA = oracle.analysis_update(dXB, dXB, M)
+    return {"Z": rel(dev["Z"], Z), "XA": rel(dev["XA"], XA), "M": rel(dev["M"], M),
+            "increment": rel(dev["XA"] - dXB, XA - dXB)}, gamma
 
 
 def check(mode, dev, r, V, D, dXB, label):
@@ -113,3 +121,53 @@ def test_panel_single_full_size():
     V = oracle.observe_deviations(dXB, 1 << 20, 4).astype(np.float32).astype(np.float64)
     dev = run(enkf.ENKF_PANEL_BF16, r, V, D, dXB)
     check(enkf.ENKF_PANEL_BF16, dev, r, V, D, dXB, "panel_single full size")
+
+
+# ---------------------------------------------------------------------------
+# One step of iterative refinement (ENKF_FLAG_REFINE).  The correction applies the
+# stored factors, an approximate inverse whose error in range(V) is about
+# rho = u * gamma_max (u the precision of the solve's operands), so one step
+# multiplies the error of Z and M by about rho; M then comes from compensated
+# Grams of the refined Z.  Bars: PANEL_FP32 and PANEL_BF16 (rho < 0.1): X_A within
+# 1e-5 of the oracle, M within max(4e-6, 0.2 * before), Z within max(1e-7, 0.5 *
+# before).  PANEL_FP16 (u = 2^-11): the errors of Z and M must shrink where
+# rho < 1 (the medium cases below); at gamma ~ 10^4 it is not effective and is
+# not tested there.
+# ---------------------------------------------------------------------------
+GAIN_MODES = (enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP32)
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16, enkf.ENKF_PANEL_FP32])
+@pytest.mark.parametrize("nobs,nens,panel_b", [(129, 16, 8), (20011, 128, 32), (9000, 256, 32), (5000, 37, 5)])
+def test_refinement_random(mode, nobs, nens, panel_b):
+    nstate = 3 * nobs + 1
+    r, V, D, dXB = problem(9100 + nobs + nens, nobs, nens, nstate)
+    base, gamma = errors(run(mode, r, V, D, dXB, panel_b), r, V, D, dXB)
+    ref, _ = errors(run(mode, r, V, D, dXB, panel_b, flags=enkf.ENKF_FLAG_REFINE), r, V, D, dXB)
+    print(f"refine {mode} nobs={nobs} nens={nens} gamma_max={gamma.max():.0f}: before " +
+          ", ".join(f"{k} {v:.2e}" for k, v in base.items()) + " | after " +
+          ", ".join(f"{k} {v:.2e}" for k, v in ref.items()))
+    if mode in GAIN_MODES:
+        assert ref["XA"] <= 1e-5, ref
+        assert ref["M"] <= max(4e-6, 0.2 * base["M"]), (base, ref)
+        assert ref["Z"] <= max(1e-7, 0.5 * base["Z"]), (base, ref)
+    else:
+        assert ref["Z"] <= 0.1 * base["Z"], (base, ref)
+        assert ref["M"] <= 0.5 * base["M"], (base, ref)
+        assert ref["XA"] <= base["XA"], (base, ref)
+
+
+@pytest.mark.parametrize("mode", GAIN_MODES)
+def test_refinement_large_single_full_size(mode):
+    w = synth.large_single(dtype=np.float32)
+    dXB = w["dXB"].astype(np.float64)
+    r = w["r"].astype(np.float64)
+    D = w["D"].astype(np.float64)
+    V = oracle.observe_deviations(dXB, w["nobs"], 4).astype(np.float32).astype(np.float64)
+    base, gamma = errors(run(mode, r, V, D, dXB), r, V, D, dXB)
+    errs, _ = errors(run(mode, r, V, D, dXB, flags=enkf.ENKF_FLAG_REFINE), r, V, D, dXB)
+    print(f"refine {mode} large_single gamma_max={gamma.max():.0f}: before " +
+          ", ".join(f"{k} {v:.2e}" for k, v in base.items()) + " | after " +
+          ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert errs["XA"] <= 1e-5, errs
+    assert errs["M"] <= max(4e-6, 0.2 * base["M"]), (base, errs)
