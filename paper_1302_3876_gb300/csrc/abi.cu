@@ -342,7 +342,8 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.rows_per_blk = p->P.rows_per_blk;
         pa.panel_b = p->panel_b;
         pa.check = a.check;
-        pa.vec_ok = (((uintptr_t)a.U | (uintptr_t)a.Z | (uintptr_t)V) % 16 == 0) && (a.ldu % 4 == 0) &&
+        pa.vec_ok = (((uintptr_t)a.U | (uintptr_t)a.Z | (uintptr_t)V | (uintptr_t)D) % 16 == 0) && (a.ldu % 4 == 0) &&
+                    (ldd % 4 == 0) &&
                     (a.ldz % 4 == 0) && (ldv % 4 == 0) && (p->P.rows_per_blk % 4 == 0);
         pa.timeout_ns = a.timeout_ns;
         pa.refine = 0;

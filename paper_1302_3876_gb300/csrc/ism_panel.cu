@@ -37,14 +37,17 @@ constexpr int XLD = RT + 4; // padded tile stride (keeps 16-byte alignment)
 constexpr int kScratch = 256 * 16;   // floats: A tile of W' (kPB*CT) or the GEMM2 row-half combine (256*16)
 
 struct PanelSmem {
-    double* G;      // [kPB][kPB]
-    double* beta;   // [kPB][kPB]
-    double* Bm;     // [kPB][kPB]
-    double* L;      // [kPB][kPB]
+    // factor temporaries (alias the X tiles, dead between sweeps)
+    float* Gh;      // [kPB][kPB]  panel Gram, hi part (float)
+    float* Gl;      // [kPB][kPB]  panel Gram, lo part: G = Gh + Gl to ~2^-48
+    float* Bt;      // [kPB][kPB]  Bt[m][u] = B[u][m]
+    float* cb;      // [kPB]       one column of beta
+    // persistent through the sweep
+    float* Lt;      // [kPB][kPB]  Lt[l][m] = L[m][l] (strictly lower part of G B)
     double* gam;    // [kPB]
     double* red;    // [32]
     float* W;       // [kPB][kPB]
-    float* Bf;      // [kPB][kPB]  gamma_m B[:,m] (for the final panel columns)
+    float* Bf;      // [kPB][kPB]  beta[u][m] = gamma_m B[u][m] (for the final panel columns)
     float* Wt;      // [kPB][CT]   W' = W A[:, tile]
     float* Xs;      // [CT][XLD]
     float* UPs;     // [kPB][RT]
@@ -70,57 +73,133 @@ __device__ __forceinline__ int trail_col(int a, int N, int k1) {
     return a < nu ? k1 + a : N + (a - nu);
 }
 
-// b x b factor from the panel Gram G by one warp; lanes own columns j.  The level
-// denominators gamma_m = 1 + (G beta_m)_m are formed in FP64 from the FP64 Gram;
-// the coefficient vectors beta, B, L and W are carried in FP32 (they only scale
-// FP32 updates; FP64 work on them would occupy the narrow FP64 pipe for ~60 us
-// per panel).
+// Knuth's TwoSum with explicitly rounded operations: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// W = B (I + L)^{-1} by backward substitution, lane q < bp forming row q:
+//   W[q][l] = B[q][l] - sum_{m > l} W[q][m] L[m][l].  Reads Bt and Lt, writes W.
+__device__ void panel_w(const PanelSmem& s, int bp) {
+    const int q = threadIdx.x & 31;
+    if (q < bp) {
+        float w[kPB];
+#pragma unroll
+        for (int l = kPB - 1; l >= 0; --l) {
+            if (l < bp) {
+                float v = s.Bt[l * kPB + q];
+#pragma unroll
+                for (int m = l + 1; m < kPB; ++m)
+                    if (m < bp) v = fmaf(-s.Lt[l * kPB + m], w[m], v);
+                w[l] = v;
+                s.W[q * kPB + l] = v;
+            } else {
+                w[l] = 0.f;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// b x b factor from the panel Gram G = Gh + Gl by one warp; lane j keeps the
+// coefficient vector beta_j (u_j = U_P beta_j) in registers.  Per level m:
+//   g_j = (G beta_j)_m (FP32), gamma_m = 1 + (G beta_m)_m in double-FP32 (exact
+//   products, TwoSum butterfly over the lanes), B[:,m] = beta_m / gamma_m,
+//   beta_j -= B[:,m] g_j (j > m).
+// Then L = strictly lower part of G B and W = B (I + L)^{-1}.  No FP64 arithmetic:
+// on GB300 a warp-wide FP64 instruction occupies the FP64 pipe for ~64 cycles.
+// gamma is written to s.gam (FP64) and the final beta to s.Bf.
 __device__ void factor_warp(const PanelSmem& s, int bp) {
     const int lane = threadIdx.x & 31;
-    float* beta = reinterpret_cast<float*>(s.beta);    // [kPB][kPB] float view of the FP64 scratch
-    float* Bm = reinterpret_cast<float*>(s.Bm);
-    float* Gf = reinterpret_cast<float*>(s.Bm) + kPB * kPB;
-    for (int e = lane; e < bp * kPB; e += 32) Gf[e] = (float)s.G[e];
-    __syncwarp();
+    float beta[kPB];
+#pragma unroll
+    for (int u = 0; u < kPB; ++u) beta[u] = (u == lane) ? 1.f : 0.f;
+    float ghi_l = 0.f, glo_l = 0.f, ginv_l = 0.f;   // gamma of this lane's level
     for (int m = 0; m < bp; ++m) {
-        const int j = lane;
-        float gm = 0.f;
-        if (j >= m && j < bp)
-            for (int u = 0; u < bp; ++u) gm = fmaf(Gf[m * kPB + u], beta[u * kPB + j], gm);
-        // gamma_m in FP64: 1 + sum_u G[m][u] beta[u][m]
-        double gmm = 0.0;
-        if (lane == 0)
-            for (int u = 0; u < bp; ++u) gmm += s.G[m * kPB + u] * (double)beta[u * kPB + m];
-        gmm = __shfl_sync(0xffffffffu, gmm, 0);
-        const double gam = 1.0 + gmm;
-        if (lane == 0) s.gam[m] = gam;
-        const float ginv = (float)(1.0 / gam);
-        if (lane < bp) Bm[lane * kPB + m] = beta[lane * kPB + m] * ginv;
-        __syncwarp();
-        if (j > m && j < bp)
-            for (int u = 0; u < bp; ++u) beta[u * kPB + j] = fmaf(-Bm[u * kPB + m], gm, beta[u * kPB + j]);
-        __syncwarp();
-    }
-    for (int m = 0; m < bp; ++m) {
-        const int l = lane;
-        float v = 0.f;
-        if (l < m)
-            for (int u = 0; u < bp; ++u) v = fmaf(Gf[m * kPB + u], Bm[u * kPB + l], v);
-        if (l < bp) s.L[m * kPB + l] = (l < m) ? (double)v : 0.0;
-    }
-    __syncwarp();
-    if (lane < bp) {
-        const int q = lane;
-        float wr[kPB];
-        for (int l = bp - 1; l >= 0; --l) {
-            float v = Bm[q * kPB + l];
-            for (int m = l + 1; m < bp; ++m) v = fmaf(-(float)s.L[m * kPB + l], wr[m], v);
-            wr[l] = v;
-            s.W[q * kPB + l] = v;
+        const float* gr = s.Gh + m * kPB;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPB; u += 4) {
+            const float4 gv = *reinterpret_cast<const float4*>(gr + u);
+            g0 = fmaf(gv.x, beta[u], g0);
+            g1 = fmaf(gv.y, beta[u + 1], g1);
+            g2 = fmaf(gv.z, beta[u + 2], g2);
+            g3 = fmaf(gv.w, beta[u + 3], g3);
         }
-        for (int m = 0; m < bp; ++m) s.Bf[q * kPB + m] = (float)((double)Bm[q * kPB + m] * s.gam[m]);
+        const float gj = (g0 + g1) + (g2 + g3);
+        if (lane == m) {
+#pragma unroll
+            for (int u = 0; u < kPB; ++u) s.cb[u] = beta[u];
+        }
+        __syncwarp();
+        // gamma_m = 1 + sum_u G[m][u] beta[u][m]: lane u forms its term exactly as hi + lo
+        const float bu = s.cb[lane];
+        const float gh = gr[lane];
+        float hi = __fmul_rn(gh, bu);
+        float lo = __fmaf_rn(gh, bu, -hi);
+        lo = __fmaf_rn(s.Gl[m * kPB + lane], bu, lo);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            float t, e;
+            two_sum(hi, h2, t, e);
+            hi = t;
+            lo = __fadd_rn(__fadd_rn(lo, l2), e);
+        }
+        float g_hi, e1;
+        two_sum(1.f, hi, g_hi, e1);
+        float g_lo = __fadd_rn(lo, e1);
+        const float tmp = __fadd_rn(g_hi, g_lo);            // renormalise (|g_lo| << |g_hi|)
+        g_lo = __fsub_rn(g_lo, __fsub_rn(tmp, g_hi));
+        g_hi = tmp;
+        const float ginv = 1.0f / g_hi;
+        if (lane == m) ghi_l = g_hi, glo_l = g_lo, ginv_l = ginv;
+        // B[:,m] = beta_m / gamma_m, kept transposed
+        s.Bt[m * kPB + lane] = bu * ginv;
+        __syncwarp();
+        if (lane > m && lane < bp) {
+            const float* bm = s.Bt + m * kPB;
+#pragma unroll
+            for (int u = 0; u < kPB; u += 4) {
+                const float4 bv = *reinterpret_cast<const float4*>(bm + u);
+                beta[u] = fmaf(-bv.x, gj, beta[u]);
+                beta[u + 1] = fmaf(-bv.y, gj, beta[u + 1]);
+                beta[u + 2] = fmaf(-bv.z, gj, beta[u + 2]);
+                beta[u + 3] = fmaf(-bv.w, gj, beta[u + 3]);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane < bp) {
+        s.gam[lane] = (double)ghi_l + (double)glo_l;
+        // final beta_l (= gamma_l B[:,l]) for the panel's own columns; B[:,l] = beta_l / gamma_l
+#pragma unroll
+        for (int u = 0; u < kPB; ++u) s.Bf[u * kPB + lane] = beta[u];
+        // L[m][l] = sum_u G[m][u] B[u][l] for m > l (lane l)
+        float bl[kPB];
+#pragma unroll
+        for (int u = 0; u < kPB; ++u) bl[u] = beta[u] * ginv_l;
+        for (int m = 0; m < bp; ++m) {
+            float v = 0.f;
+            if (m > lane) {
+                const float* gr = s.Gh + m * kPB;
+#pragma unroll
+                for (int u = 0; u < kPB; u += 4) {
+                    const float4 gv = *reinterpret_cast<const float4*>(gr + u);
+                    v = fmaf(gv.x, bl[u], v);
+                    v = fmaf(gv.y, bl[u + 1], v);
+                    v = fmaf(gv.z, bl[u + 2], v);
+                    v = fmaf(gv.w, bl[u + 3], v);
+                }
+            }
+            s.Lt[lane * kPB + m] = v;
+        }
     }
     __syncwarp();
+    panel_w(s, bp);
 }
 
 // Cross-CTA sum of the partial dots in a fixed order: each CTA owns a slice of the
@@ -137,8 +216,21 @@ __device__ bool reduce_panel(const PanelArgs& a, const PanelSmem& s, int nvals, 
         const int teams = kPT / ne;
         const int t = threadIdx.x, e = t % ne, g = t / ne;
         double v = 0.0;
-        if (g < teams && e0 + eb + e < nvals)
-            for (unsigned b = g; b < nblk; b += teams) v += __ldcg(&a.part[(int64_t)b * a.part_stride + e0 + eb + e]);
+        if (g < teams && e0 + eb + e < nvals) {
+            const double* src = a.part + e0 + eb + e;
+            unsigned b = g;
+            for (; b + 3 * teams < nblk; b += 4 * teams) {   // four loads in flight, summed in order
+                const double x0 = __ldcg(src + (int64_t)b * a.part_stride);
+                const double x1 = __ldcg(src + (int64_t)(b + teams) * a.part_stride);
+                const double x2 = __ldcg(src + (int64_t)(b + 2 * teams) * a.part_stride);
+                const double x3 = __ldcg(src + (int64_t)(b + 3 * teams) * a.part_stride);
+                v += x0;
+                v += x1;
+                v += x2;
+                v += x3;
+            }
+            for (; b < nblk; b += teams) v += __ldcg(src + (int64_t)b * a.part_stride);
+        }
         __syncthreads();
         sub[t] = v;
         __syncthreads();
@@ -185,6 +277,53 @@ __device__ __forceinline__ void stage_cols(float* dst, int ld, int ncols_tile, i
     }
 }
 
+// Sweep options.
+constexpr int kMaterialize = 1;   // write the panel's final U columns (last column tile)
+constexpr int kStep1 = 2;         // first sweep: stage V and D, apply Step 1, write U and Z
+
+// Step 1 (eq. SM-step-1) on a staged tile: x[c][j] = x[c][j] / r_j.
+__device__ __forceinline__ void scale_tile(float* xs, const float* r, int64_t row0, int nr) {
+    const int j = threadIdx.x & 63;
+    if (j < nr) {
+        const float rj = r[row0 + j];
+        for (int c = threadIdx.x >> 6; c < CT; c += kPT / 64) xs[c * XLD + j] = xs[c * XLD + j] / rj;
+    }
+}
+
+// Writes the ncl columns of a staged tile back to rows [row0, row0 + nr): 16-byte stores along rows.
+template <bool VEC, typename ColFn>
+__device__ __forceinline__ void writeback_tile(const float* xs, int ncl, int64_t row0, int nr, ColFn col) {
+    for (int e = threadIdx.x; e < CT * (RT / 4); e += kPT) {
+        const int c = e >> 4, j4 = (e & 15) * 4;
+        if (c >= ncl) continue;
+        float* dst = col(c) + row0 + j4;
+        const float4 v = *reinterpret_cast<const float4*>(&xs[c * XLD + j4]);
+        if (VEC && j4 + 4 <= nr) {
+            *reinterpret_cast<float4*>(dst) = v;
+        } else {
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+            for (int q = 0; q < 4; ++q)
+                if (j4 + q < nr) dst[q] = vv[q];
+        }
+    }
+}
+
+// Final values of the panel's own columns on one row tile: u_{k0+m}^(k0+m-1) =
+// gamma_m U_P B[:,m] = U_P beta_m, from the U_P rows staged in shared memory
+// (ups: [t][row]).  Called in the sweep's last column tile, when no later stage
+// reads these rows of U_P.
+__device__ __forceinline__ void materialize_tile(const PanelArgs& a, const PanelSmem& s, const float* ups, int k0,
+                                                 int bp, int64_t row0, int nr) {
+    static_assert(RT == 64, "row index mapping");
+    for (int e = threadIdx.x; e < bp * RT; e += kPT) {
+        const int m = e >> 6, j = e & 63;
+        if (j >= nr) continue;
+        float v = 0.f;
+        for (int u = 0; u <= m; ++u) v = fmaf(ups[u * RT + j], s.Bf[u * kPB + m], v);
+        col_ptr(a, k0 + m)[row0 + j] = v;
+    }
+}
+
 // One sweep over this CTA's rows for the panel [k0, k0+bp) (bp = 0: no update) and
 // the next panel [k1, k1+nb) (nb = 0: no dots).  A (reduced dots of the previous
 // sweep) is read from coefg with row stride ncols_prev = ncols + bp.
@@ -192,13 +331,16 @@ __device__ __forceinline__ void stage_cols(float* dst, int ld, int ncols_tile, i
 // loads of 16 lanes fall in distinct banks.
 template <bool VEC>
 __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
-                        int kv, int nb, int aoff, bool materialize) {
+                        int kv, int nb, int aoff, int opts) {
     const int N = a.nens;
     const int k1 = ku;   // trailing U columns start here (N: none)
     const int ncols = (N - k1) + N;
     const int ncols_prev = ncols + aoff;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float* V = static_cast<const float*>(a.V);
+    const float* D = static_cast<const float*>(a.D);
+    const float* r = static_cast<const float*>(a.r);
+    const bool step1 = (opts & kStep1) != 0;
     const int ntiles = (int)((nrows + RT - 1) / RT);
     // GEMM2 mapping: columns cq + 16 q, dot rows tq*4 + s, row half
     const int cq = tid & 15, tq = (tid >> 4) & 7, half = tid >> 7;
@@ -226,6 +368,11 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
         auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
+        auto scol = [&](int c) -> const float* {       // staging source: V / D for the Step-1 sweep
+            const int cc = trail_col(c0 + c, N, k1);
+            if (!step1) return col_ptr(a, cc);
+            return cc < N ? V + (int64_t)cc * a.ldv : D + (int64_t)(cc - N) * a.ldd;
+        };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
         auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
         auto stage = [&](int tile, int buf) {
@@ -233,7 +380,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
             float* xs = s.Xs + buf * CT * XLD;
-            stage_cols<VEC>(xs, XLD, CT, ncl, row0, nr, xcol);
+            stage_cols<VEC>(xs, XLD, CT, ncl, row0, nr, scol);
             if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
             if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
             cp_async_commit();
@@ -254,6 +401,11 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
             const float* vns = s.VNs + buf * kPB * RT;
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
+            if (step1) {
+                scale_tile(xs, r, r0 + rr, nr);
+                __syncthreads();
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+            }
             if (bp > 0) {
                 // GEMM1: rows 4 ty.., columns tx + 16 q
                 float x[4][4];
@@ -277,20 +429,8 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
                     *reinterpret_cast<float4*>(&xs[(tx + 16 * q) * XLD + ty * 4]) =
                         make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
                 __syncthreads();
-                // write the updated tile back: 16-byte stores along rows
-                for (int e = tid; e < CT * (RT / 4); e += kPT) {
-                    const int c = e >> 4, j4 = (e & 15) * 4;
-                    if (c >= ncl) continue;
-                    float* dst = xcol(c) + r0 + rr + j4;
-                    const float4 v = *reinterpret_cast<const float4*>(&xs[c * XLD + j4]);
-                    if (VEC && j4 + 4 <= nr) {
-                        *reinterpret_cast<float4*>(dst) = v;
-                    } else {
-                        const float vv[4] = {v.x, v.y, v.z, v.w};
-                        for (int q = 0; q < 4; ++q)
-                            if (j4 + q < nr) dst[q] = vv[q];
-                    }
-                }
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+                if ((opts & kMaterialize) && c0 + CT >= ncols) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
             }
             if (nb > 0 && tq * 4 < nb) {
                 // GEMM2: acc[s][q] += sum_j VN[tq*4+s][j] X[cq+16q][j] over this thread's row half
@@ -334,25 +474,6 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
                                    (double)(acc[s4][q] + red[tid * 16 + s4 * 4 + q]));
                     }
                 }
-            }
-        }
-    }
-    // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
-    if (bp > 0 && materialize) {
-        for (int64_t rr = 0; rr < nrows; rr += RT) {
-            const int nr = (int)min((int64_t)RT, nrows - rr);
-            const int64_t row0 = r0 + rr;
-            __syncthreads();
-            for (int e = tid; e < bp * RT; e += kPT) {
-                const int t = e >> 6, j = e & 63;
-                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
-            }
-            __syncthreads();
-            for (int e = tid; e < bp * RT; e += kPT) {
-                const int m = e >> 6, j = e & 63;
-                float v = 0.f;
-                for (int u = 0; u <= m; ++u) v = fmaf(s.UPs[u * RT + j], s.Bf[u * kPB + m], v);
-                if (j < nr) col_ptr(a, k0 + m)[row0 + j] = v;
             }
         }
     }
@@ -425,7 +546,7 @@ __device__ __forceinline__ void put4(unsigned short* h, unsigned short* l, float
 
 template <bool VEC, int PREC>
 __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
-                         int kv, int nb, int aoff, bool materialize) {
+                         int kv, int nb, int aoff, int opts) {
     constexpr bool SPLIT = Tc<PREC>::split;
     const int N = a.nens;
     const int k1 = ku;
@@ -433,6 +554,9 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
     const int ncols_prev = ncols + aoff;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float* V = static_cast<const float*>(a.V);
+    const float* D = static_cast<const float*>(a.D);
+    const float* r = static_cast<const float*>(a.r);
+    const bool step1 = (opts & kStep1) != 0;
     const int ntiles = (int)((nrows + RT - 1) / RT);
     const int j8 = lane >> 3;
     for (int c0 = 0; c0 < ncols; c0 += CT) {
@@ -462,13 +586,18 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
 #pragma unroll
             for (int h = 0; h < 4; ++h) acc2[mt][h] = 0.f;
         auto xcol = [&](int c) { return col_ptr(a, trail_col(c0 + c, N, k1)); };
+        auto scol = [&](int c) -> const float* {       // staging source: V / D for the Step-1 sweep
+            const int cc = trail_col(c0 + c, N, k1);
+            if (!step1) return col_ptr(a, cc);
+            return cc < N ? V + (int64_t)cc * a.ldv : D + (int64_t)(cc - N) * a.ldd;
+        };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
         auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
-            stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, xcol);
+            stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, scol);
             if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
             if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
             cp_async_commit();
@@ -489,6 +618,10 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
             const float* vns = s.VNs + buf * kPB * RT;
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
+            if (step1) {
+                scale_tile(xs, r, r0 + rr, nr);
+                __syncthreads();
+            }
             // 16-bit operand tiles: -U_P [t][row], V' [t][row] (zero rows t >= bp / nb)
             for (int e = tid; e < kPB * (RT / 4); e += kPT) {
                 const int t = e >> 4, r4 = (e & 15) * 4;
@@ -558,20 +691,10 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                         if (SPLIT) s.Xl[col * HP + row] = Tc<PREC>::hi(v - Tc<PREC>::back(hv));
                     }
                 __syncthreads();
-                for (int e = tid; e < CT * (RT / 4); e += kPT) {
-                    const int c = e >> 4, j4 = (e & 15) * 4;
-                    if (c >= ncl) continue;
-                    float* dst = xcol(c) + r0 + rr + j4;
-                    const float4 v = *reinterpret_cast<const float4*>(&xs[c * XLD + j4]);
-                    if (VEC && j4 + 4 <= nr) {
-                        *reinterpret_cast<float4*>(dst) = v;
-                    } else {
-                        const float vv[4] = {v.x, v.y, v.z, v.w};
-                        for (int q = 0; q < 4; ++q)
-                            if (j4 + q < nr) dst[q] = vv[q];
-                    }
-                }
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+                if ((opts & kMaterialize) && c0 + CT >= ncols) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
             }
+            if (step1) writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
             if (nb > 0) {
                 // GEMM2: warp -> columns warp*8.. (one n-tile), t = 0..31 (two m-tiles), K = 64 rows
 #pragma unroll
@@ -611,25 +734,6 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                 }
         }
     }
-    // final values of the panel's own columns: u_m^(m-1) = gamma_m U_P B[:,m]
-    if (bp > 0 && materialize) {
-        for (int64_t rr = 0; rr < nrows; rr += RT) {
-            const int nr = (int)min((int64_t)RT, nrows - rr);
-            const int64_t row0 = r0 + rr;
-            __syncthreads();
-            for (int e = tid; e < bp * RT; e += kPT) {
-                const int t = e >> 6, j = e & 63;
-                s.UPs[t * RT + j] = j < nr ? col_ptr(a, k0 + t)[row0 + j] : 0.f;
-            }
-            __syncthreads();
-            for (int e = tid; e < bp * RT; e += kPT) {
-                const int m = e >> 6, j = e & 63;
-                float v = 0.f;
-                for (int u = 0; u <= m; ++u) v = fmaf(s.UPs[u * RT + j], s.Bf[u * kPB + m], v);
-                if (j < nr) col_ptr(a, k0 + m)[row0 + j] = v;
-            }
-        }
-    }
 }
 
 // Sweep over this CTA's rows: update the trailing columns (u_ku.., all z) with the
@@ -638,17 +742,17 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
 // the panel's final U columns.
 template <int PREC>
 __device__ void sweep(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
-                      int kv, int nb, int aoff, bool materialize) {
+                      int kv, int nb, int aoff, int opts) {
     if (PREC == 0) {
         if (a.vec_ok)
-            sweep_t<true>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
+            sweep_t<true>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, opts);
         else
-            sweep_t<false>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
+            sweep_t<false>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, opts);
     } else {
         if (a.vec_ok)
-            sweep_tc<true, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
+            sweep_tc<true, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, opts);
         else
-            sweep_tc<false, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, materialize);
+            sweep_tc<false, PREC == 0 ? 1 : PREC>(a, s, r0, nrows, k0, bp, ku, kv, nb, aoff, opts);
     }
 }
 
@@ -662,34 +766,28 @@ __device__ void refine_body(const PanelArgs& a, const PanelSmem& s, int64_t r0, 
     const int N = a.nens, b = a.panel_b;
     const int tid = threadIdx.x;
     int nb = b < N ? b : N;
-    sweep<0>(a, s, r0, nrows, 0, 0, N, 0, nb, 0, false);
+    sweep<0>(a, s, r0, nrows, 0, 0, N, 0, nb, 0, 0);
     if (!reduce_panel(a, s, nb * N, epoch)) return;
     for (int k0 = 0; k0 < N; k0 += b) {
         const int bp = (N - k0) < b ? (N - k0) : b;
         const int k1 = k0 + bp;
         if (tid < 32) {
-            // gamma' and L of this panel from the Gram, then W = diag(1/gamma') (I + L)^{-1}
-            for (int m = tid; m < bp; m += 32) s.gam[m] = 1.0 + a.Qg[(int64_t)(k0 + m) * N + (k0 + m)];
-            __syncwarp();
-            for (int e = tid; e < bp * bp; e += 32) {
-                const int m = e / bp, l = e % bp;
-                s.L[m * kPB + l] = (l < m) ? a.Qg[(int64_t)(k0 + m) * N + (k0 + l)] / s.gam[l] : 0.0;
-            }
-            __syncwarp();
-            const int q = tid;
-            if (q < bp) {
-                float tcol[kPB];
+            // gamma'_l = 1 + Q[l][l] and L[m][l] = Q[m][l] / gamma'_l (lane l), B = diag(1/gamma'),
+            // then W = B (I + L)^{-1}
+            const int l = tid;
+            if (l < bp) {
+                const double ginv = 1.0 / (1.0 + a.Qg[(int64_t)(k0 + l) * N + (k0 + l)]);
                 for (int m = 0; m < bp; ++m) {
-                    float v = (m == q) ? 1.f : 0.f;
-                    for (int l = q; l < m; ++l) v = fmaf(-(float)s.L[m * kPB + l], tcol[l], v);
-                    tcol[m] = (m < q) ? 0.f : v;
+                    s.Lt[l * kPB + m] = m > l ? (float)(a.Qg[(int64_t)(k0 + m) * N + (k0 + l)] * ginv) : 0.f;
+                    s.Bt[m * kPB + l] = m == l ? (float)ginv : 0.f;
                 }
-                for (int m = 0; m < bp; ++m) s.W[m * kPB + q] = (float)((double)tcol[m] / s.gam[m]);
             }
+            __syncwarp();
+            panel_w(s, bp);
         }
         __syncthreads();
         nb = (N - k1) < b ? (N - k1) : b;
-        sweep<0>(a, s, r0, nrows, k0, bp, N, k1, nb, 0, false);
+        sweep<0>(a, s, r0, nrows, k0, bp, N, k1, nb, 0, 0);
         if (nb > 0) {
             if (!reduce_panel(a, s, nb * N, epoch)) return;
         } else {
@@ -704,8 +802,8 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     // persistent: L, gamma, W, Bf, W'; tile buffers; the factor's temporaries G, beta, B
     // alias the X tile buffers (they are dead between sweeps)
     PanelSmem s;
-    s.L = reinterpret_cast<double*>(smem_raw);
-    s.gam = s.L + kPB * kPB;
+    s.Lt = reinterpret_cast<float*>(smem_raw);
+    s.gam = reinterpret_cast<double*>(s.Lt + kPB * kPB);
     s.red = s.gam + kPB;
     s.W = reinterpret_cast<float*>(s.red + 32);
     s.Bf = s.W + kPB * kPB;
@@ -714,9 +812,10 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     s.UPs = s.Xs + 2 * CT * XLD;
     s.VNs = s.UPs + 2 * kPB * RT;
     s.flag = reinterpret_cast<int*>(s.VNs + 2 * kPB * RT + kScratch);
-    s.G = reinterpret_cast<double*>(s.Xs);
-    s.beta = s.G + kPB * kPB;
-    s.Bm = s.beta + kPB * kPB;
+    s.Gh = s.Xs;
+    s.Gl = s.Gh + kPB * kPB;
+    s.Bt = s.Gl + kPB * kPB;
+    s.cb = s.Bt + kPB * kPB;
     {
         unsigned short* h = reinterpret_cast<unsigned short*>(s.flag + 4);
         s.Uh = h; h += kPB * HP;
@@ -728,7 +827,7 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
         s.Vh = h; h += kPB * HP;
         s.Vl = h;
     }
-    static_assert(3 * kPB * kPB * sizeof(double) <= 2 * CT * XLD * sizeof(float), "factor temporaries fit the tiles");
+    static_assert(3 * kPB * kPB + kPB <= 2 * CT * XLD, "factor temporaries fit the tiles");
 
     const int N = a.nens, b = a.panel_b;
     const int tid = threadIdx.x;
@@ -736,72 +835,65 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     const int64_t r1 = min(r0 + (int64_t)a.rows_per_blk, a.nobs);
     const int64_t nrows = r1 > r0 ? r1 - r0 : 0;
     unsigned epoch = 0;
-    const float* V = static_cast<const float*>(a.V);
-    const float* D = static_cast<const float*>(a.D);
     const float* r = static_cast<const float*>(a.r);
 
     if (a.refine) {   // correction sweep: U holds the final columns, Z the scaled residual
         refine_body(a, s, r0, nrows, epoch);
         return;
     }
-    // ---- Step 1 (eq. SM-step-1) on this CTA's rows
-    for (int c = tid / 64; c < 2 * N; c += kPT / 64) {
-        const float* src = c < N ? V + (int64_t)c * a.ldv : D + (int64_t)(c - N) * a.ldd;
-        float* dst = col_ptr(a, c);
-        for (int64_t j = tid % 64; j < nrows; j += 64) {
+    // ---- Step 1 (eq. SM-step-1), U = R^-1 V and Z = R^-1 D, is applied by the first sweep
+    if (a.check)
+        for (int64_t j = tid; j < nrows; j += kPT) {
             const float rj = r[r0 + j];
-            if (a.check && !(rj > 0.f && isfinite(rj))) {
+            if (!(rj > 0.f && isfinite(rj))) {
                 set_status(a.ctl, kErrNumeric);
                 a.ctl->fail_level = 0;
             }
-            dst[r0 + j] = src[r0 + j] / rj;
         }
-    }
     __syncthreads();
-    // ---- dots of panel 0 with every column
+    // ---- Step 1 and the dots of panel 0 with every column
     int nb = b < N ? b : N;
-    sweep<PREC>(a, s, r0, nrows, 0, 0, 0, 0, nb, 0, true);
+    sweep<PREC>(a, s, r0, nrows, 0, 0, 0, 0, nb, 0, kStep1);
     if (!reduce_panel(a, s, nb * 2 * N, epoch)) return;
 
     for (int k0 = 0; k0 < N; k0 += b) {
         const int bp = (N - k0) < b ? (N - k0) : b;
         const int k1 = k0 + bp;
         const int ncols_prev = (N - k0) + N;
-        // factor of the panel (every CTA, FP64)
-        for (int e = tid; e < bp * bp; e += kPT) {
-            const int t = e / bp, u = e % bp;
-            s.G[t * kPB + u] = __ldcg(&a.coefg[t * ncols_prev + u]);
-            reinterpret_cast<float*>(s.beta)[t * kPB + u] = (t == u) ? 1.f : 0.f;
+        // factor of the panel (every CTA): the FP64 Gram split into float hi + lo
+        for (int e = tid; e < kPB * kPB; e += kPT) {
+            const int t = e / kPB, u = e % kPB;
+            const double g = (t < bp && u < bp) ? __ldcg(&a.coefg[t * ncols_prev + u]) : 0.0;
+            const float h = (float)g;
+            s.Gh[e] = h;
+            s.Gl[e] = (float)(g - (double)h);
         }
         __syncthreads();
         if (tid < 32) factor_warp(s, bp);
         __syncthreads();
-        if (blockIdx.x == 0) {
-            // gamma and the per-level Z coefficients c = (I + L)^{-1} a for every z column
-            if (tid < bp) a.gamma[k0 + tid] = s.gam[tid];
-            for (int i = tid; i < N; i += kPT) {
-                const int ai = (N - k0) + i;   // index of z_i among the previous sweep's columns
-                float c[kPB];
-                for (int m = 0; m < bp; ++m) {
-                    float v = (float)__ldcg(&a.coefg[m * ncols_prev + ai]);
-                    for (int l = 0; l < m; ++l) v = fmaf(-(float)s.L[m * kPB + l], c[l], v);
-                    c[m] = v;
-                    a.C[(int64_t)(k0 + m) * N + i] = (double)v;
-                }
+        if (blockIdx.x == 0 && tid < bp) {
+            const double g = s.gam[tid];
+            a.gamma[k0 + tid] = g;
+            if (a.check && (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g))) {
+                set_status(a.ctl, kErrNumeric);
+                a.ctl->fail_level = k0 + tid + 1;
             }
-            if (a.check && tid == 0) {
-                for (int m = 0; m < bp; ++m) {
-                    const double g = s.gam[m];
-                    if (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g)) {
-                        set_status(a.ctl, kErrNumeric);
-                        a.ctl->fail_level = k0 + m + 1;
-                    }
-                }
+        }
+        // per-level Z coefficients c = (I + L)^{-1} a of z_i (one warp per column, CTAs
+        // round-robin over the columns): lane m holds a_m, level l broadcasts c_l
+        for (int i = blockIdx.x * (kPT / 32) + (tid >> 5); i < N; i += gridDim.x * (kPT / 32)) {
+            const int lane = tid & 31;
+            const int ai = (N - k0) + i;   // index of z_i among the previous sweep's columns
+            float v = lane < bp ? (float)__ldcg(&a.coefg[lane * ncols_prev + ai]) : 0.f;
+            for (int l = 0; l < bp; ++l) {
+                const float cl = __shfl_sync(0xffffffffu, v, l);
+                if (lane > l) v = fmaf(-s.Lt[l * kPB + lane], cl, v);
             }
+            if (lane < bp) a.C[(int64_t)(k0 + lane) * N + i] = (double)v;
         }
         nb = (N - k1) < b ? (N - k1) : b;
         // every CTA has read coefg; it is rewritten only after the next barrier
-        sweep<PREC>(a, s, r0, nrows, k0, bp, k1, k1, nb, bp, true);
+        sweep<PREC>(a, s, r0, nrows, k0, bp, k1, k1, nb, bp, kMaterialize);
         if (nb > 0) {
             if (!reduce_panel(a, s, nb * ((N - k1) + N), epoch)) return;
         } else {
@@ -811,8 +903,8 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
 }
 
 size_t panel_smem(int prec) {
-    const size_t base = sizeof(double) * (kPB * kPB + kPB + 32) +
-                        sizeof(float) * (2 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
+    const size_t base = sizeof(double) * (kPB + 32) +
+                        sizeof(float) * (3 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
     const size_t tc = sizeof(unsigned short) * 2 * (2 * kPB * HP + CT * WPT + CT * HP);
     return base + (prec ? tc : 0);
 }

@@ -33,6 +33,7 @@ BARS = {
     enkf.ENKF_PANEL_FP16: {"Z": 5e-3, "XA": 1e-3, "M": 2e-3},
 }
 NAME = {enkf.ENKF_PANEL_BF16: "PANEL_BF16", enkf.ENKF_PANEL_FP16: "PANEL_FP16"}
+GAMMA_REL = {enkf.ENKF_PANEL_BF16: 1e-4, enkf.ENKF_PANEL_FP16: 1e-3}   # ~ 2^-17 and 2^-11 operands
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -87,7 +88,8 @@ def check(mode, dev, r, V, D, dXB, label):
     assert errs["Z"] <= bar["Z"], errs
     assert errs["XA"] <= bar["XA"], errs
     assert errs["M"] <= bar["M"] * max(1.0, gamma.max() / 10.0), errs
-    assert dev["info"].gamma_max == pytest.approx(gamma.max(), rel=1e-4)
+    # the level denominators inherit the operand precision of the panel Gram
+    assert dev["info"].gamma_max == pytest.approx(gamma.max(), rel=GAMMA_REL[mode])
 
 
 @pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16])
