@@ -161,7 +161,7 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_Q = o; o = align256(o + sizeof(double) * N * N);
     p->off_M = o; o = align256(o + p->w * N * N);
     p->off_M64 = o; o = align256(o + sizeof(double) * N * N);
-    p->off_Msplit = o; o = align256(o + 2 * sizeof(uint16_t) * N * (size_t)xa_tc_kpad(nens));
+    p->off_Msplit = o; o = align256(o + xa_split_bytes(nens));
     p->refine = panel && (flags & ENKF_FLAG_REFINE);
     if (p->refine) {
         p->off_delta = o; o = align256(o + sizeof(float) * (size_t)p->ldzw * N);
@@ -403,9 +403,9 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             if (p->fp64)
                 CU(xa_update(true, p->nstate, p->nens, XB, ldb, dXB, ldx, Mp, XA, lda, s), "xa_update launch");
             else
-                CU(xa_update_tc(p->nstate, p->nens, (const float*)XB, ldb, (const float*)dXB, ldx, (const float*)Mp,
-                                ws + p->off_Msplit, (float*)XA, lda, s),
-                   "xa_update_tc launch");
+                CU(xa_update_tc05(p->nstate, p->nens, (const float*)XB, ldb, (const float*)dXB, ldx, (const float*)Mp,
+                                  ws + p->off_Msplit, (float*)XA, lda, ctl, a.timeout_ns, s),
+                   "xa_update_tc05 launch");
             prof_end(p, slot, s);
         }
     }

@@ -27,11 +27,21 @@ constexpr int GT = 64;   // tile edge
 constexpr int GR = 32;   // rows per smem stage
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_upper_kernel(int64_t nrows, int n, const T* __restrict__ A, int64_t lda,
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(sizeof(T)),
+                 "r"(valid ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) gram_upper_kernel(int64_t nrows, int n, const T* __restrict__ A, int64_t lda,
                                                          const T* __restrict__ B, int64_t ldb, int64_t rows_per_split,
                                                          double* __restrict__ Qpart, int full) {
-    __shared__ T As[GT][GR + 1];
-    __shared__ T Bs[GT][GR + 1];
+    // two stages of SR rows x 64 columns of A and B, [column][row] (odd row pitch: conflict-free)
+    constexpr int SR = sizeof(T) == 8 ? GR / 2 : GR;
+    __shared__ T As[2][GT][SR + 1];
+    __shared__ T Bs[2][GT][SR + 1];
     // map blockIdx.x to a tile: every (kb, mb) when full, else the upper tiles (kb <= mb)
     const int nt = (n + GT - 1) / GT;
     int kb = 0, mb = 0;
@@ -56,33 +66,45 @@ __global__ void __launch_bounds__(256) gram_upper_kernel(int64_t nrows, int n, c
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) accd[i][q] = 0.0, acc[i][q] = T(0);
-    int stage = 0;
-    for (int64_t jb = j0; jb < j1; jb += GR) {
-        __syncthreads();
-        // load 32 rows x 64 columns of A and B: lane -> row, warp and step -> column
-        const int lr = tid & 31;
-        for (int c = tid >> 5; c < GT; c += 8) {
-            const int64_t j = jb + lr;
+    // asynchronous copies of one stage: lane -> row (coalesced), warp and step -> column
+    auto stage = [&](int64_t jb, int buf) {
+        const int lr = tid % SR;
+        const int64_t j = jb + lr;
+        for (int c = tid / SR; c < GT; c += 256 / SR) {
             const int ka = kb * GT + c, mbc = mb * GT + c;
-            As[c][lr] = (j < j1 && ka < n) ? A[(int64_t)ka * lda + j] : T(0);
-            Bs[c][lr] = (j < j1 && mbc < n) ? B[(int64_t)mbc * ldb + j] : T(0);
+            const bool va = j < j1 && ka < n, vb = j < j1 && mbc < n;
+            cp_async_elem(&As[buf][c][lr], va ? A + (int64_t)ka * lda + j : A, va);
+            cp_async_elem(&Bs[buf][c][lr], vb ? B + (int64_t)mbc * ldb + j : B, vb);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int stage_no = 0;
+    if (j0 < j1) stage(j0, 0);
+    for (int64_t jb = j0; jb < j1; jb += SR) {
+        const int buf = (int)(((jb - j0) / SR) & 1);
+        if (jb + SR < j1) {
+            stage(jb + SR, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
 #pragma unroll 8
-        for (int j = 0; j < GR; ++j) {
+        for (int j = 0; j < SR; ++j) {
             T a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[ty * 4 + i][j];
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][ty * 4 + i][j];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = Bs[tx * 4 + q][j];
+            for (int q = 0; q < 4; ++q) b[q] = Bs[buf][tx * 4 + q][j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[i][q] += a[i] * b[q];
         }
-        // fold the working-precision accumulators into double every 16 stages (512 rows)
-        if (++stage == 16) {
-            stage = 0;
+        __syncthreads();     // the buffer is refilled by the next iteration's prefetch
+        // fold the working-precision accumulators into double every 512 rows
+        if (++stage_no == 512 / SR) {
+            stage_no = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -186,161 +208,6 @@ __global__ void __launch_bounds__(256) xa_update_kernel(int64_t nstate, int n, c
     }
 }
 
-// ---------------------------------------------------------------------------
-// XA = XB + dXB * M on BF16 tensor cores with split operands (FP32 storage):
-// dXB = A_hi + A_lo and M = M_hi + M_lo (BF16 each), XA = XB + A_hi M_hi + A_hi M_lo
-// + A_lo M_hi (the dropped A_lo M_lo term is below FP32 rounding), FP32 accumulation
-// (mma.sync m16n8k16).  CTA tile 128 rows x 128 columns, 8 warps of 32 x 64, K in
-// chunks of 32; A chunks are staged [k][row] (fragments by ldmatrix.trans), M is
-// pre-split into [col][k] hi/lo (ldmatrix).  X_B initialises the accumulators.
-// ---------------------------------------------------------------------------
-constexpr int TR = 128, TC = 128, KC = 32;
-constexpr int APITCH = TR + 8;     // bf16, [k][row]
-constexpr int BPITCH = KC + 8;     // bf16, [col][k]
-
-__global__ void split_M_kernel(const float* __restrict__ M, int n, int kpad, __nv_bfloat16* __restrict__ Mhi,
-                               __nv_bfloat16* __restrict__ Mlo) {
-    // Mhi/Mlo[e][k] = split of M[k + e n] (k < n), zero for k >= n
-    const int64_t total = (int64_t)n * kpad;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int e = (int)(q / kpad), k = (int)(q % kpad);
-        const float v = k < n ? M[k + (int64_t)e * n] : 0.f;
-        const __nv_bfloat16 h = __float2bfloat16(v);
-        Mhi[q] = h;
-        Mlo[q] = __float2bfloat16(v - __bfloat162float(h));
-    }
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__global__ void __launch_bounds__(256) xa_update_tc_kernel(int64_t nstate, int n, int kpad, const float* XB,
-                                                           int64_t ldb, const float* __restrict__ dXB, int64_t ldx,
-                                                           const __nv_bfloat16* __restrict__ Mhi,
-                                                           const __nv_bfloat16* __restrict__ Mlo, float* XA,
-                                                           int64_t lda, int vec_a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(smem_raw);   // [KC][APITCH]
-    __nv_bfloat16* Alo = Ahi + KC * APITCH;
-    __nv_bfloat16* Bhi = Alo + KC * APITCH;                              // [TC][BPITCH]
-    __nv_bfloat16* Blo = Bhi + TC * BPITCH;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp & 3) * 32, wn = (warp >> 2) * 64;
-    const int e0 = blockIdx.y * TC;
-    const int64_t ntiles = (nstate + TR - 1) / TR;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i0 = tile * TR;
-        float acc[2][8][4];
-        // accumulators start at X_B
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int64_t i = i0 + wm + mt * 16 + (lane >> 2) + (h >> 1) * 8;
-                    const int e = e0 + wn + nt * 8 + (lane & 3) * 2 + (h & 1);
-                    acc[mt][nt][h] = (i < nstate && e < n) ? XB[(int64_t)e * ldb + i] : 0.f;
-                }
-        for (int k0 = 0; k0 < kpad; k0 += KC) {
-            __syncthreads();
-            // A chunk: dXB rows i0.., members k0..k0+31 -> [k][row] hi/lo
-            for (int q = tid; q < KC * (TR / 4); q += 256) {
-                const int k = q / (TR / 4), r4 = (q % (TR / 4)) * 4;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                if (k0 + k < n) {
-                    const float* src = dXB + (int64_t)(k0 + k) * ldx + i0 + r4;
-                    if (vec_a && i0 + r4 + 3 < nstate) {
-                        const float4 f = *reinterpret_cast<const float4*>(src);
-                        v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
-                    } else {
-                        for (int u = 0; u < 4; ++u)
-                            if (i0 + r4 + u < nstate) v[u] = src[u];
-                    }
-                }
-                __align__(8) __nv_bfloat16 h[4], l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h[u] = __float2bfloat16(v[u]);
-                    l[u] = __float2bfloat16(v[u] - __bfloat162float(h[u]));
-                }
-                *reinterpret_cast<uint2*>(Ahi + k * APITCH + r4) = *reinterpret_cast<const uint2*>(h);
-                *reinterpret_cast<uint2*>(Alo + k * APITCH + r4) = *reinterpret_cast<const uint2*>(l);
-            }
-            // B chunk: [col][k] hi/lo for columns e0.., k0..k0+31 (16-byte copies)
-            for (int q = tid; q < TC * (KC / 8); q += 256) {
-                const int c = q / (KC / 8), k8 = (q % (KC / 8)) * 8;
-                uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
-                if (e0 + c < n) {
-                    vh = *reinterpret_cast<const uint4*>(Mhi + (int64_t)(e0 + c) * kpad + k0 + k8);
-                    vl = *reinterpret_cast<const uint4*>(Mlo + (int64_t)(e0 + c) * kpad + k0 + k8);
-                }
-                *reinterpret_cast<uint4*>(Bhi + c * BPITCH + k8) = vh;
-                *reinterpret_cast<uint4*>(Blo + c * BPITCH + k8) = vl;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < KC; kk += 16) {
-                uint32_t ah[2][4], al[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    // matrices (m 0-7,k 0-7) (m 8-15,k 0-7) (m 0-7,k 8-15) (m 8-15,k 8-15) from [k][row]
-                    const int j = lane >> 3;
-                    const int kr = kk + (j >> 1) * 8 + (lane & 7);
-                    const int mr = wm + mt * 16 + (j & 1) * 8;
-                    ldsm_x4_t(ah[mt], Ahi + kr * APITCH + mr);
-                    ldsm_x4_t(al[mt], Alo + kr * APITCH + mr);
-                }
-#pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    // two n-tiles: matrices (n 0-7,k 0-7) (n 0-7,k 8-15) (n 8-15,k 0-7) (n 8-15,k 8-15)
-                    const int j = lane >> 3;
-                    const int nr = wn + np * 16 + (j >> 1) * 8 + (lane & 7);
-                    const int kc = kk + (j & 1) * 8;
-                    uint32_t bh[4], bl[4];
-                    ldsm_x4(bh, Bhi + nr * BPITCH + kc);
-                    ldsm_x4(bl, Blo + nr * BPITCH + kc);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            float* d = acc[mt][np * 2 + hh];
-                            mma16816(d, al[mt], bh[2 * hh], bh[2 * hh + 1]);
-                            mma16816(d, ah[mt], bl[2 * hh], bl[2 * hh + 1]);
-                            mma16816(d, ah[mt], bh[2 * hh], bh[2 * hh + 1]);
-                        }
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int64_t i = i0 + wm + mt * 16 + (lane >> 2) + (h >> 1) * 8;
-                    const int e = e0 + wn + nt * 8 + (lane & 3) * 2 + (h & 1);
-                    if (i < nstate && e < n) XA[(int64_t)e * lda + i] = acc[mt][nt][h];
-                }
-    }
-}
-
 }  // namespace
 
 int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
@@ -412,37 +279,6 @@ cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, i
         xa_update_kernel<float><<<grid, 256, smem, s>>>(nstate, nens, (const float*)XB, ldb, (const float*)dXB, ldx,
                                                         (const float*)M, (float*)XA, lda);
     }
-    return cudaGetLastError();
-}
-
-}  // namespace enkf
-
-namespace enkf {
-
-int32_t xa_tc_kpad(int32_t nens) { return (nens + KC - 1) / KC * KC; }
-
-cudaError_t xa_update_tc(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
-                         const float* M, void* msplit, float* XA, int64_t lda, cudaStream_t s) {
-    const int kpad = xa_tc_kpad(nens);
-    __nv_bfloat16* Mhi = static_cast<__nv_bfloat16*>(msplit);
-    __nv_bfloat16* Mlo = Mhi + (size_t)nens * kpad;
-    split_M_kernel<<<(int)(((int64_t)nens * kpad + 255) / 256), 256, 0, s>>>(M, nens, kpad, Mhi, Mlo);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(__nv_bfloat16) * (2 * KC * APITCH + 2 * TC * BPITCH);
-    if ((e = cudaFuncSetAttribute(xa_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return e;
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t ntiles = (nstate + TR - 1) / TR;
-    const int ycols = (nens + TC - 1) / TC;
-    int64_t gx = (int64_t)nsm * 3 / ycols;
-    if (gx < 1) gx = 1;
-    if (gx > ntiles) gx = ntiles;
-    const int vec_a = ((uintptr_t)dXB % 16 == 0) && (ldx % 4 == 0);
-    xa_update_tc_kernel<<<dim3((unsigned)gx, (unsigned)ycols), 256, smem, s>>>(nstate, nens, kpad, XB, ldb, dXB, ldx,
-                                                                               Mhi, Mlo, XA, lda, vec_a);
     return cudaGetLastError();
 }
 

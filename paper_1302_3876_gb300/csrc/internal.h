@@ -119,11 +119,13 @@ cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C
 cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, int64_t ldb,
                       const void* dXB, int64_t ldx, const void* M, void* XA, int64_t lda, cudaStream_t s);
 
-// XA = XB + dXB * M on BF16 tensor cores with split (hi + lo) operands, FP32 storage.
-// msplit: workspace of 2 * nens * xa_tc_kpad(nens) bf16 (the split copy of M).
-int32_t xa_tc_kpad(int32_t nens);
-cudaError_t xa_update_tc(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
-                         const float* M, void* msplit, float* XA, int64_t lda, cudaStream_t s);
+// X_A = X_B + dX_B M on tcgen05 tensor cores (split BF16 operands, FP32 accumulators
+// in TMEM); msplit: xa_split_bytes(nens) bytes of workspace (the split images of M);
+// waits are bounded by timeout_ns and latch kErrTimeout in ctl.
+size_t xa_split_bytes(int32_t nens);
+cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
+                           const float* M, void* msplit, float* XA, int64_t lda, Control* ctl, uint64_t timeout_ns,
+                           cudaStream_t s);
 
 // Observation-space preparation.
 cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int32_t stride, int32_t center,

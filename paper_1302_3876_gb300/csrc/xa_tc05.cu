@@ -1,0 +1,487 @@
+// X_A = X_B + dX_B M (the SMEnKF analysis update, Sec. 3.1) on the fifth-generation
+// tensor cores: tcgen05.mma with BF16 operands split as x = hi + lo, three products
+// (hi*hi + hi*lo + lo*hi; lo*lo is below FP32 rounding), FP32 accumulators in TMEM.
+//
+// Persistent, warp-specialised CTA, one per SM; a tile is 128 state rows x NB members:
+//   warp 16     loader: TMA tensor copies of the FP32 dX_B chunk (128 rows x 32 members)
+//               into a ring of raw slots (mbarrier transaction counts).
+//   warps 8-15  converters: raw FP32 -> BF16 hi/lo in the K-major canonical layout of
+//               the MMA (core matrices of 8 rows x 16 bytes; LBO 128 B along K, SBO 256 B
+//               along rows) in a ring of operand slots.  Without TMA (unaligned dX_B)
+//               they read dX_B from global memory themselves.
+//   warp 17     TMEM allocation and the MMA issue (one thread): 2 K-steps x 3 products
+//               per chunk; tcgen05.commit frees the operand slot, and after a tile's last
+//               chunk marks its accumulator full.  Two accumulators in TMEM.
+//   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4).. (its 32 rows) for one
+//               half of the columns; X_A = X_B + acc with coalesced column accesses.
+// M is pre-split into hi/lo images of the same layout; they stay in shared memory for
+// the whole launch when they fit (Nens <= 128), else each chunk's part travels in the
+// operand slot.  Every mbarrier wait is bounded (iteration count and %globaltimer); on
+// expiry the CTA latches ENKF_ERR_TIMEOUT, drains its copies and MMAs with bounded
+// waits, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace enkf {
+namespace {
+
+constexpr int XM = 128;     // rows per tile (MMA M)
+constexpr int XKC = 32;     // K per chunk: two MMA K-steps of 16
+constexpr int XRS = 4;      // raw (FP32) slots
+constexpr int XNMAX = 256;  // largest MMA N
+constexpr int kEpi = 256, kConv = 256;
+constexpr int kThreads = kEpi + kConv + 64;    // + loader warp + MMA warp
+constexpr int kRawBytes = XM * XKC * 4;        // one raw chunk
+constexpr int kABytes = 2 * XM * XKC * 2;      // A hi + lo of one chunk
+constexpr int kMaxSmem = 232448;
+
+__host__ __device__ constexpr int b_chunk_bytes(int nb) { return 2 * nb * XKC * 2; }   // B hi + lo of one chunk
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+struct XaShared {
+    uint64_t raw_full[XRS], raw_empty[XRS], a_full[4], a_empty[4], acc_full[2], acc_empty[2], drained;
+    unsigned taddr;
+    int err;
+};
+
+// Bounded wait for the phase of `parity`; false (CTA error flag and device status
+// latched) once it gives up or another role already has.
+__device__ bool mbar_wait(uint64_t* bar, unsigned parity, XaShared* sh, Control* ctl, uint64_t timeout_ns) {
+    const uint64_t t0 = global_timer_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*(volatile int*)&sh->err) return false;
+            if (global_timer_ns() - t0 > timeout_ns || it > (1u << 26)) {
+                *(volatile int*)&sh->err = 1;
+                set_status(ctl, kErrTimeout);
+                return false;
+            }
+        }
+    }
+}
+// Wait bounded by time only (draining after an error).
+__device__ void mbar_drain(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try(bar, parity) && global_timer_ns() - t0 < timeout_ns) {
+    }
+}
+
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    // tcgen05 shared-memory matrix descriptor: start >> 4 [0,14), leading byte offset >> 4
+    // [16,30) (between core matrices along K), stride byte offset >> 4 [32,46) (between
+    // 8-row groups), descriptor version 1 at [46,48), no swizzle.
+    const uint64_t a = (smem_u32(p) >> 4) & 0x3FFFu;
+    return a | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 at [17,23), M >> 4 at [24,29).
+__device__ __forceinline__ unsigned instr_desc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(XM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// 8 consecutive k of one row -> hi and lo 16-byte rows of their core matrices.
+__device__ __forceinline__ void put_row8(unsigned char* ahi, int off, const float* v) {
+    uint4 h, l;
+    h.x = pack_bf16(v[0], v[1]);
+    h.y = pack_bf16(v[2], v[3]);
+    h.z = pack_bf16(v[4], v[5]);
+    h.w = pack_bf16(v[6], v[7]);
+    const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
+    float lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) lo[q] = v[q] - __bfloat162float(hb[q]);
+    l.x = pack_bf16(lo[0], lo[1]);
+    l.y = pack_bf16(lo[2], lo[3]);
+    l.z = pack_bf16(lo[4], lo[5]);
+    l.w = pack_bf16(lo[6], lo[7]);
+    *reinterpret_cast<uint4*>(ahi + off) = h;
+    *reinterpret_cast<uint4*>(ahi + XM * XKC * 2 + off) = l;
+}
+
+struct XaParams {
+    int64_t nstate;
+    int nens, nb, nchunks, alloc_cols, nas, resident;
+    const float* XB;
+    int64_t ldb;
+    const float* dXB;
+    int64_t ldx;
+    const uint4* Mimg;
+    float* XA;
+    int64_t lda;
+    Control* ctl;
+    uint64_t timeout_ns;
+};
+
+template <bool TMA>
+__global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_constant__ CUtensorMap tmap, XaParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const int nb = p.nb, nchunks = p.nchunks, nas = p.nas;
+    const int aslot = kABytes + (p.resident ? 0 : b_chunk_bytes(nb));
+    // 1024-byte aligned working area (the launch reserves 1 KB of slack for this)
+    unsigned char* raw = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // XRS x kRawBytes
+    unsigned char* aring = raw + XRS * kRawBytes;                    // nas x aslot
+    unsigned char* bres = aring + nas * aslot;                       // resident B images
+    XaShared* sh = reinterpret_cast<XaShared*>(bres + (p.resident ? nchunks * b_chunk_bytes(nb) : 0));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int yb = blockIdx.y;
+    const int64_t ntiles = (p.nstate + XM - 1) / XM;
+
+    if (tid == 0) {
+        for (int q = 0; q < XRS; ++q) mbar_init(&sh->raw_full[q], 1), mbar_init(&sh->raw_empty[q], kConv);
+        for (int q = 0; q < nas; ++q) mbar_init(&sh->a_full[q], kConv), mbar_init(&sh->a_empty[q], 1);
+        for (int q = 0; q < 2; ++q) mbar_init(&sh->acc_full[q], 1), mbar_init(&sh->acc_empty[q], kEpi);
+        mbar_init(&sh->drained, 1);
+        sh->err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 17) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sh->taddr)),
+                     "r"(p.alloc_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tbase = sh->taddr;
+
+    if (warp == 16) {
+        // ---------------- loader (TMA)
+        if (TMA && lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int rs = (int)(g % XRS);
+                    if (g >= XRS && !mbar_wait(&sh->raw_empty[rs], (unsigned)((g / XRS - 1) & 1), sh, p.ctl,
+                                               p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&sh->raw_full[rs], kRawBytes);
+                    const int x = (int)(tile * XM), y = c * XKC;
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3}], [%4];\n" ::"r"(smem_u32(raw + rs * kRawBytes)),
+                        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y), "r"(smem_u32(&sh->raw_full[rs]))
+                        : "memory");
+                }
+            }
+            // every issued copy has landed before the CTA may exit
+            for (int64_t f = g - 1; f >= 0 && f >= g - XRS; --f)   // the last fill of each slot
+                mbar_drain(&sh->raw_full[f % XRS], (unsigned)((f / XRS) & 1), p.timeout_ns);
+        }
+    } else if (warp >= 8 && warp < 16) {
+        // ---------------- converters
+        const int ct = tid - kEpi;
+        const int r = ct & (XM - 1), kh = ct >> 7;     // row, half of the chunk's 32 k
+        if (p.resident) {
+            const uint4* src = p.Mimg + (int64_t)yb * nchunks * (b_chunk_bytes(nb) / 16);
+            uint4* dst = reinterpret_cast<uint4*>(bres);
+            for (int q = ct; q < nchunks * b_chunk_bytes(nb) / 16; q += kConv) dst[q] = __ldg(src + q);
+        }
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const int64_t i = tile * XM + r;
+            for (int c = 0; c < nchunks; ++c, ++g) {
+                const int s = (int)(g % nas), rs = (int)(g % XRS);
+                if (g >= nas && !mbar_wait(&sh->a_empty[s], (unsigned)((g / nas - 1) & 1), sh, p.ctl, p.timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                float v[16];
+                if (TMA) {
+                    if (!mbar_wait(&sh->raw_full[rs], (unsigned)((g / XRS) & 1), sh, p.ctl, p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const float* rw = reinterpret_cast<const float*>(raw + rs * kRawBytes);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = rw[(kh * 16 + q) * XM + r];
+                    mbar_arrive(&sh->raw_empty[rs]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int k = c * XKC + kh * 16 + q;
+                        v[q] = (i < p.nstate && k < p.nens) ? __ldg(p.dXB + (int64_t)k * p.ldx + i) : 0.f;
+                    }
+                }
+                unsigned char* slot = aring + s * aslot;
+                // K-step kh, k-groups 0 and 1: core (r / 8, kg), row r % 8
+                const int off = kh * (XM * 32) + (r >> 3) * 256 + (r & 7) * 16;
+                put_row8(slot, off, v);
+                put_row8(slot, off + 128, v + 8);
+                if (!p.resident) {
+                    const uint4* src = p.Mimg + ((int64_t)yb * nchunks + c) * (b_chunk_bytes(nb) / 16);
+                    uint4* dst = reinterpret_cast<uint4*>(slot + kABytes);
+                    for (int q = ct; q < b_chunk_bytes(nb) / 16; q += kConv) dst[q] = __ldg(src + q);
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&sh->a_full[s]);
+            }
+        }
+    } else if (warp < 8) {
+        // ---------------- epilogue
+        const int quarter = warp & 3, half = warp >> 2;
+        const int ngroups = nb / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+        int64_t t = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+            const int b = (int)(t & 1);
+            if (!mbar_wait(&sh->acc_full[b], (unsigned)((t >> 1) & 1), sh, p.ctl, p.timeout_ns)) break;
+            tc_fence_after();
+            const int64_t i = tile * XM + quarter * 32 + lane;
+            const unsigned row_addr = tbase + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * nb);
+            for (int gq = g0; gq < g1; ++gq) {
+                const int e0 = yb * nb + gq * 16;
+                float xb[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    xb[q] = (i < p.nstate && e0 + q < p.nens) ? p.XB[(int64_t)(e0 + q) * p.ldb + i] : 0.f;
+                unsigned acc[16];
+                tmem_ld16(row_addr + gq * 16, acc);
+                tmem_wait_ld();
+                if (i < p.nstate) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sh->acc_empty[b]);
+        }
+    } else {
+        // ---------------- MMA issue (warp 17, one thread)
+        if (lane == 0) {
+            const unsigned idesc = instr_desc(nb);
+            int64_t g = 0, t = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++t) {
+                const int b = (int)(t & 1);
+                if (t >= 2 && !mbar_wait(&sh->acc_empty[b], (unsigned)(((t >> 1) - 1) & 1), sh, p.ctl, p.timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned dcol = tbase + (unsigned)(b * nb);
+                for (int c = 0; c < nchunks; ++c, ++g) {
+                    const int s = (int)(g % nas);
+                    if (!mbar_wait(&sh->a_full[s], (unsigned)((g / nas) & 1), sh, p.ctl, p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char* ahi = aring + s * aslot;
+                    const unsigned char* alo = ahi + XM * XKC * 2;
+                    const unsigned char* bhi = p.resident ? bres + c * b_chunk_bytes(nb) : ahi + kABytes;
+                    const unsigned char* blo = bhi + nb * XKC * 2;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const int aoff = ks * XM * 32, boff = ks * nb * 32;
+                        const int first = (c == 0 && ks == 0);
+                        mma_bf16(dcol, smem_desc(alo + aoff), smem_desc(bhi + boff), idesc, first ? 0 : 1);
+                        mma_bf16(dcol, smem_desc(ahi + aoff), smem_desc(blo + boff), idesc, 1);
+                        mma_bf16(dcol, smem_desc(ahi + aoff), smem_desc(bhi + boff), idesc, 1);
+                    }
+                    mma_commit(&sh->a_empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&sh->acc_full[b]);
+            }
+            // the commit arrives once every MMA issued above has completed
+            mma_commit(&sh->drained);
+            mbar_drain(&sh->drained, 0u, p.timeout_ns);
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 17) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(p.alloc_cols)
+                     : "memory");
+    }
+}
+
+// M (column-major [k + e n]) -> the per-chunk canonical images: for column block yb
+// and chunk c, hi then lo, each [ks][n / 8][kg][n % 8][8 k] of BF16.
+__global__ void xa_tc05_image_kernel(const float* __restrict__ M, int n, int nb, int nblocks, int nchunks,
+                                     __nv_bfloat16* __restrict__ img) {
+    const int64_t per = (int64_t)nb * XKC;               // elements of one hi (or lo) chunk
+    const int64_t total = (int64_t)nblocks * nchunks * per;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = q / per;                     // yb * nchunks + c
+        const int rem = (int)(q % per);
+        const int yb = (int)(blk / nchunks), c = (int)(blk % nchunks);
+        const int ks = rem / (nb * 16), r2 = rem % (nb * 16);
+        const int ng = r2 / 128, r3 = r2 % 128;
+        const int kg = r3 / 64, r4 = r3 % 64;
+        const int rn = r4 / 8, kk = r4 % 8;
+        const int e = yb * nb + ng * 8 + rn;             // member (column of X_A)
+        const int k = c * XKC + ks * 16 + kg * 8 + kk;   // member of dX_B (row of M)
+        const float v = (e < n && k < n) ? M[k + (int64_t)e * n] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16(v);
+        img[blk * 2 * per + rem] = h;
+        img[blk * 2 * per + per + rem] = __float2bfloat16(v - __bfloat162float(h));
+    }
+}
+
+struct XaGeom {
+    int nb, nblocks, nchunks, alloc, nas, resident, smem;
+};
+
+XaGeom xa_geom(int32_t nens) {
+    XaGeom g;
+    const int nfirst = nens < XNMAX ? nens : XNMAX;
+    g.nb = (nfirst + 15) / 16 * 16;
+    g.nblocks = (nens + g.nb - 1) / g.nb;
+    g.nchunks = (nens + XKC - 1) / XKC;
+    int alloc = 32;
+    while (alloc < 2 * g.nb) alloc *= 2;
+    g.alloc = alloc;
+    g.resident = g.nchunks * b_chunk_bytes(g.nb) <= 65536;
+    const int aslot = kABytes + (g.resident ? 0 : b_chunk_bytes(g.nb));
+    const int fixed = XRS * kRawBytes + (g.resident ? g.nchunks * b_chunk_bytes(g.nb) : 0) + (int)sizeof(XaShared) + 1024;
+    g.nas = (kMaxSmem - fixed) / aslot;
+    if (g.nas > 4) g.nas = 4;
+    g.smem = fixed + g.nas * aslot;
+    // one CTA per SM (the two accumulators may take all 512 TMEM columns)
+    if (g.smem < kMaxSmem / 2 + 1024) g.smem = kMaxSmem / 2 + 1024;
+    return g;
+}
+
+}  // namespace
+
+size_t xa_split_bytes(int32_t nens) {
+    const XaGeom g = xa_geom(nens);
+    return (size_t)g.nblocks * g.nchunks * b_chunk_bytes(g.nb);
+}
+
+cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
+                           const float* M, void* msplit, float* XA, int64_t lda, Control* ctl, uint64_t timeout_ns,
+                           cudaStream_t s) {
+    const XaGeom g = xa_geom(nens);
+    if (g.nas < 2) return cudaErrorInvalidConfiguration;
+    {
+        const int64_t total = (int64_t)g.nblocks * g.nchunks * g.nb * XKC;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        xa_tc05_image_kernel<<<blocks, 256, 0, s>>>(M, nens, g.nb, g.nblocks, g.nchunks,
+                                                     static_cast<__nv_bfloat16*>(msplit));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // TMA tensor map of dX_B (rows inner, members outer), box 128 rows x 32 members; the
+    // rows and members past the end read as zeros.  Needs 16-byte aligned base and stride.
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    bool tma = ((uintptr_t)dXB % 16 == 0) && ((ldx * 4) % 16 == 0) && nstate < (int64_t(1) << 31);
+    if (tma) {
+        const cuuint64_t dims[2] = {(cuuint64_t)nstate, (cuuint64_t)nens};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+        const cuuint32_t box[2] = {XM, XKC};
+        const cuuint32_t estr[2] = {1, 1};
+        // resolved through the runtime so the library has no link-time dependency on libcuda
+        using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                         CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                         CUtensorMapFloatOOBfill);
+        static EncodeTiled encode = nullptr;
+        if (!encode) {
+            void* f = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                encode = reinterpret_cast<EncodeTiled>(f);
+        }
+        tma = encode && encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(dXB), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const void* fn = tma ? (const void*)xa_tc05_kernel<true> : (const void*)xa_tc05_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t ntiles = (nstate + XM - 1) / XM;
+    int64_t gx = (int64_t)nsm / g.nblocks;
+    if (gx < 1) gx = 1;
+    if (gx > ntiles) gx = ntiles;
+    XaParams p;
+    p.nstate = nstate;
+    p.nens = nens;
+    p.nb = g.nb;
+    p.nchunks = g.nchunks;
+    p.alloc_cols = g.alloc;
+    p.nas = g.nas;
+    p.resident = g.resident;
+    p.XB = XB;
+    p.ldb = ldb;
+    p.dXB = dXB;
+    p.ldx = ldx;
+    p.Mimg = static_cast<const uint4*>(msplit);
+    p.XA = XA;
+    p.lda = lda;
+    p.ctl = ctl;
+    p.timeout_ns = timeout_ns;
+    void* args[] = {&tmap, &p};
+    return cudaLaunchKernel(fn, dim3((unsigned)gx, (unsigned)g.nblocks), dim3(kThreads), args, g.smem, s);
+}
+
+}  // namespace enkf
