@@ -9,7 +9,8 @@
 //   panel P = {k0, .., k0+b-1}, trailing columns x = u_i (i >= k0+b) and all z_i:
 //     a = V_P^T x                     (b dots per column, accumulated in the previous sweep)
 //     G = V_P^T U_P                   (the same dots for the panel's own columns)
-//     b x b recurrence in FP64 (eqs. SM-step-2-h/u restricted to the panel):
+//     b x b recurrence (eqs. SM-step-2-h/u restricted to the panel; FP32 coefficient
+//     vectors, gamma in double-FP32 -- the factor shared with the single-problem kernel):
 //       gamma_m = 1 + (G beta_m)_m,   B[:,m] = beta_m / gamma_m,
 //       beta_j <- beta_j - B[:,m] (G beta_j)_m   (j > m),      so h_m = U_P B[:,m];
 //     c_m = v_m^T x^(m-1) = a_m - sum_{l<m} (G B)[m,l] c_l,  i.e. c = (I + L)^{-1} a;
@@ -30,6 +31,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "panel_factor.cuh"
 
 namespace enkf {
 namespace {
@@ -40,16 +42,18 @@ constexpr int kBmax = 32;     // largest panel width
 struct SmemB {
     float* apart;      // [kBT][kBmax]   per-thread partial dots
     float* A;          // [kBmax][256]   reduced dots a_t of each active column
-    double* G;         // [kBmax][kBmax] panel Gram (FP64)
-    double* beta;      // [kBmax][kBmax]
-    double* Bm;        // [kBmax][kBmax]
-    double* L;         // [kBmax][kBmax]
+    float* Gh;         // [kBmax][kBmax] panel Gram G = V_P^T U_P (Gl = 0: FP32 dots)
+    float* Gl;         // [kBmax][kBmax]
+    float* Bt;         // [kBmax][kBmax] Bt[m][u] = B[u][m]
+    float* cb;         // [kBmax]
+    float* Lt;         // [kBmax][kBmax] Lt[l][m] = L[m][l]
     float* W;          // [kBmax][kBmax] W = B (I + L)^{-1}
-    float* Bf;         // [kBmax][kBmax] gamma_m B[:,m] (final panel columns)
-    float* tile;       // [32][33] transpose tile
+    float* Bf;         // [kBmax][kBmax] beta[u][m] = gamma_m B[u][m] (final panel columns)
+    float* tile;       // [2][32][33] transpose tiles
     double* gam;       // [kBmax]
     int* flag;         // [4]
 };
+static_assert(kBmax == kFB, "panel factor width");
 
 __device__ __forceinline__ int col_of(int a, int N, int k1) {
     // trailing columns after panel ending at k1: u_{k1..N-1}, then z_{0..N-1}
@@ -121,23 +125,53 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
         }
     }
     __syncthreads();   // s.A is rewritten below
-    if (active) {
-        const int col = col_of(a, N, k1);
-        int cnt = 0;
-        for (int j = g; j < n; j += G) {
-            float x = X[(int64_t)j * ldX + col];
+    // rows in blocks of 32: the panel rows of U_P and V_{P'} are staged in shared memory
+    // (zero beyond bp / nb) and read as broadcasts, four per 16-byte load
+    float* Us = s.tile;                 // [32][B]
+    float* Vs = s.tile + 32 * kBmax;    // [32][B]
+    const int col = active ? col_of(a, N, k1) : 0;
+    int cnt = 0;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        __syncthreads();
+        for (int e = t; e < 32 * B; e += kBT) {
+            const int jj = e / B, q = e % B, j = j0 + jj;
+            Us[e] = (update && q < bp && j < n) ? X[(int64_t)j * ldX + k0 + q] : 0.f;
+            Vs[e] = (nb > 0 && q < nb && j < n) ? Vr[(int64_t)j * ldVr + k1 + q] : 0.f;
+        }
+        __syncthreads();
+        if (!active) continue;
+        const int jend = min(32, n - j0);
+        for (int jj = g; jj < jend; jj += G) {
+            const int64_t j = j0 + jj;
+            float x = X[j * ldX + col];
             if (update) {
-                const float* up = X + (int64_t)j * ldX + k0;
 #pragma unroll
-                for (int q = 0; q < B; ++q)
-                    if (q < bp) x = fmaf(-up[q], w[q], x);
-                X[(int64_t)j * ldX + col] = x;
+                for (int q = 0; q < B; q += (B >= 4 ? 4 : 1)) {
+                    if (B >= 4) {
+                        const float4 u4 = *reinterpret_cast<const float4*>(Us + jj * B + q);
+                        x = fmaf(-u4.x, w[q], x);
+                        x = fmaf(-u4.y, w[q + 1], x);
+                        x = fmaf(-u4.z, w[q + 2], x);
+                        x = fmaf(-u4.w, w[q + 3], x);
+                    } else {
+                        x = fmaf(-Us[jj * B + q], w[q], x);
+                    }
+                }
+                X[j * ldX + col] = x;
             }
             if (nb > 0) {
-                const float* vn = Vr + (int64_t)j * ldVr + k1;
 #pragma unroll
-                for (int q = 0; q < B; ++q)
-                    if (q < nb) acc[q] = fmaf(vn[q], x, acc[q]);
+                for (int q = 0; q < B; q += (B >= 4 ? 4 : 1)) {
+                    if (B >= 4) {
+                        const float4 v4 = *reinterpret_cast<const float4*>(Vs + jj * B + q);
+                        acc[q] = fmaf(v4.x, x, acc[q]);
+                        acc[q + 1] = fmaf(v4.y, x, acc[q + 1]);
+                        acc[q + 2] = fmaf(v4.z, x, acc[q + 2]);
+                        acc[q + 3] = fmaf(v4.w, x, acc[q + 3]);
+                    } else {
+                        acc[q] = fmaf(Vs[jj * B + q], x, acc[q]);
+                    }
+                }
                 if (++cnt == 64) {
                     cnt = 0;
 #pragma unroll
@@ -145,6 +179,8 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
                 }
             }
         }
+    }
+    if (active) {
 #pragma unroll
         for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] = outer[q] + acc[q];
     }
@@ -161,60 +197,22 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
     __syncthreads();
 }
 
-// Panel factor from the Gram G = A[:, 0..bp) (FP64): gamma, B, L = (G B) strictly lower,
-// W = B (I + L)^{-1}.  Returns false (and latches kErrNumeric) on a bad gamma.
+// Panel factor from the Gram G = A[:, 0..bp): gamma, B, L = (G B) strictly lower,
+// W = B (I + L)^{-1} (factor_warp); latches kErrNumeric on a bad gamma.
 __device__ bool factor(const SmemB& s, int bp, Control* ctl, bool check) {
     const int t = threadIdx.x;
-    for (int e = t; e < bp * bp; e += kBT) {
-        const int q = e / bp, u = e % bp;
-        s.G[q * kBmax + u] = (double)s.A[q * 256 + u];      // G[t][s] = v_t^T u_s
-        s.beta[q * kBmax + u] = (q == u) ? 1.0 : 0.0;        // beta[row][col j]
+    for (int e = t; e < kBmax * kBmax; e += kBT) {
+        const int q = e / kBmax, u = e % kBmax;
+        s.Gh[e] = (q < bp && u < bp) ? s.A[q * 256 + u] : 0.f;      // G[t][s] = v_t^T u_s
+        s.Gl[e] = 0.f;
     }
     __syncthreads();
     if (t < 32) {
-        // lane j owns column beta_j; sequential over m
-        for (int m = 0; m < bp; ++m) {
-            // (G beta_j)_m for every j >= m (lane j)
-            double gm = 0.0;
-            if (t >= m && t < bp)
-                for (int u = 0; u < bp; ++u) gm += s.G[m * kBmax + u] * s.beta[u * kBmax + t];
-            const double gmm = __shfl_sync(0xffffffffu, gm, m);
-            const double gam = 1.0 + gmm;
-            if (t == 0) s.gam[m] = gam;
-            // B[:, m] = beta_m / gamma_m (lanes over rows u)
-            if (t < bp) s.Bm[t * kBmax + m] = s.beta[t * kBmax + m] / gam;
-            __syncwarp();
-            if (t > m && t < bp)
-                for (int u = 0; u < bp; ++u) s.beta[u * kBmax + t] -= s.Bm[u * kBmax + m] * gm;
-            __syncwarp();
-        }
-        // L[m][l] = (G B)[m][l], l < m; lane l
-        for (int m = 0; m < bp; ++m) {
-            double v = 0.0;
-            if (t < m)
-                for (int u = 0; u < bp; ++u) v += s.G[m * kBmax + u] * s.Bm[u * kBmax + t];
-            if (t < bp) s.L[m * kBmax + t] = (t < m) ? v : 0.0;
-        }
-        __syncwarp();
-        // W = B (I + L)^{-1}: row q of W solves W[q,:] (I + L) = B[q,:], back substitution over columns
-        if (t < bp) {
-            double wr[kBmax];
-            for (int l = bp - 1; l >= 0; --l) {
-                double v = s.Bm[t * kBmax + l];
-                for (int m = l + 1; m < bp; ++m) v -= s.L[m * kBmax + l] * wr[m];
-                wr[l] = v;
-                s.W[t * kBmax + l] = (float)v;
-            }
-        }
-        __syncwarp();
-        if (t < bp)
-            for (int m = 0; m < bp; ++m) s.Bf[t * kBmax + m] = (float)(s.Bm[t * kBmax + m] * s.gam[m]);
-        if (t == 0 && check) {
-            for (int m = 0; m < bp; ++m) {
-                const double g = s.gam[m];
-                if (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g))
-                    set_status(ctl, kErrNumeric);
-            }
+        factor_warp(s, bp);
+        if (t < bp && check) {
+            const double g = s.gam[t];
+            if (!(g >= 1.0 - 64.0 * 1.1920928955078125e-07 * (1.0 + fabs(g - 1.0))) || !isfinite(g))
+                set_status(ctl, kErrNumeric);
         }
     }
     __syncthreads();
@@ -229,9 +227,9 @@ __device__ void panel_z_coefficients(const BatchDesc& d, const SmemB& s, float* 
         float c[kBmax];
         for (int m = 0; m < bp; ++m) {
             float v = s.A[m * 256 + (N - k0) + i];
-            for (int l = 0; l < m; ++l) v = fmaf(-(float)s.L[m * kBmax + l], c[l], v);
+            for (int l = 0; l < m; ++l) v = fmaf(-s.Lt[l * kBmax + m], c[l], v);
             c[m] = v;
-            Ch[(int64_t)(k0 + m) * N + i] = (float)((double)v / s.gam[m]);
+            Ch[(int64_t)(k0 + m) * N + i] = v / (float)s.gam[m];
         }
     }
     __syncthreads();
@@ -342,7 +340,7 @@ __device__ void solve_problem(const BatchDesc& d, const float* in, float* out, f
     finish_problem(d, out, X, Vr, s.tile, Ch, ws + d.Qw);
 }
 
-__global__ void __launch_bounds__(kBT) ism_batch_kernel(const BatchDesc* __restrict__ desc,
+__global__ void __launch_bounds__(kBT, 2) ism_batch_kernel(const BatchDesc* __restrict__ desc,
                                                         const int* __restrict__ order, int nprob,
                                                         const float* in, float* out, float* ws, Control* ctl,
                                                         int check, int force_b) {
@@ -350,12 +348,13 @@ __global__ void __launch_bounds__(kBT) ism_batch_kernel(const BatchDesc* __restr
     SmemB s;
     s.apart = reinterpret_cast<float*>(smem_raw);
     s.A = s.apart + kBT * kBmax;
-    s.G = reinterpret_cast<double*>(s.A + kBmax * 256);
-    s.beta = s.G + kBmax * kBmax;
-    s.Bm = s.beta + kBmax * kBmax;
-    s.L = s.Bm + kBmax * kBmax;
-    s.gam = s.L + kBmax * kBmax;
-    s.W = reinterpret_cast<float*>(s.gam + kBmax);
+    s.gam = reinterpret_cast<double*>(s.A + kBmax * 256);
+    s.Gh = reinterpret_cast<float*>(s.gam + kBmax);
+    s.Gl = s.Gh + kBmax * kBmax;
+    s.Bt = s.Gl + kBmax * kBmax;
+    s.Lt = s.Bt + kBmax * kBmax;
+    s.cb = s.Lt + kBmax * kBmax;
+    s.W = s.cb + kBmax;
     s.Bf = s.W + kBmax * kBmax;
     s.tile = s.Bf + kBmax * kBmax;
     s.flag = reinterpret_cast<int*>(s.tile + 2 * 32 * 33);
@@ -379,8 +378,8 @@ __global__ void __launch_bounds__(kBT) ism_batch_kernel(const BatchDesc* __restr
 }  // namespace
 
 size_t batch_smem_bytes() {
-    return sizeof(float) * (size_t)kBT * kBmax + sizeof(float) * kBmax * 256 + sizeof(double) * 4 * kBmax * kBmax +
-           sizeof(double) * kBmax + 2 * sizeof(float) * kBmax * kBmax + sizeof(float) * 2 * 32 * 33 + 16;
+    return sizeof(float) * (size_t)kBT * kBmax + sizeof(float) * kBmax * 256 + sizeof(double) * kBmax +
+           sizeof(float) * (6 * kBmax * kBmax + kBmax) + sizeof(float) * 2 * 32 * 33 + 16;
 }
 
 cudaError_t batch_configure(int* grid) {

@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "panel_factor.cuh"
 
 namespace enkf {
 namespace {
@@ -53,6 +54,12 @@ struct PanelSmem {
     float* UPs;     // [kPB][RT]
     float* VNs;     // [kPB][RT]
     int* flag;      // [4]
+    // column base pointers of the current column tile (staging source, write-back
+    // destination) and of the panel's U and V columns
+    const float** psrc;   // [CT]
+    float** pdst;         // [CT]
+    float** pu;           // [kPB]
+    const float** pv;     // [kPB]
     // tensor-core variants: 16-bit operand tiles (hi, and lo for the split form)
     unsigned short *Uh, *Ul;   // [kPB][HP]   -U_P, [t][row]
     unsigned short *Wh, *Wl;   // [CT][WPT]   W',   [col][t]
@@ -71,135 +78,6 @@ __device__ __forceinline__ float* col_ptr(const PanelArgs& a, int c) {
 __device__ __forceinline__ int trail_col(int a, int N, int k1) {
     const int nu = N - k1;
     return a < nu ? k1 + a : N + (a - nu);
-}
-
-// Knuth's TwoSum with explicitly rounded operations: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// W = B (I + L)^{-1} by backward substitution, lane q < bp forming row q:
-//   W[q][l] = B[q][l] - sum_{m > l} W[q][m] L[m][l].  Reads Bt and Lt, writes W.
-__device__ void panel_w(const PanelSmem& s, int bp) {
-    const int q = threadIdx.x & 31;
-    if (q < bp) {
-        float w[kPB];
-#pragma unroll
-        for (int l = kPB - 1; l >= 0; --l) {
-            if (l < bp) {
-                float v = s.Bt[l * kPB + q];
-#pragma unroll
-                for (int m = l + 1; m < kPB; ++m)
-                    if (m < bp) v = fmaf(-s.Lt[l * kPB + m], w[m], v);
-                w[l] = v;
-                s.W[q * kPB + l] = v;
-            } else {
-                w[l] = 0.f;
-            }
-        }
-    }
-    __syncwarp();
-}
-
-// b x b factor from the panel Gram G = Gh + Gl by one warp; lane j keeps the
-// coefficient vector beta_j (u_j = U_P beta_j) in registers.  Per level m:
-//   g_j = (G beta_j)_m (FP32), gamma_m = 1 + (G beta_m)_m in double-FP32 (exact
-//   products, TwoSum butterfly over the lanes), B[:,m] = beta_m / gamma_m,
-//   beta_j -= B[:,m] g_j (j > m).
-// Then L = strictly lower part of G B and W = B (I + L)^{-1}.  No FP64 arithmetic:
-// on GB300 a warp-wide FP64 instruction occupies the FP64 pipe for ~64 cycles.
-// gamma is written to s.gam (FP64) and the final beta to s.Bf.
-__device__ void factor_warp(const PanelSmem& s, int bp) {
-    const int lane = threadIdx.x & 31;
-    float beta[kPB];
-#pragma unroll
-    for (int u = 0; u < kPB; ++u) beta[u] = (u == lane) ? 1.f : 0.f;
-    float ghi_l = 0.f, glo_l = 0.f, ginv_l = 0.f;   // gamma of this lane's level
-    for (int m = 0; m < bp; ++m) {
-        const float* gr = s.Gh + m * kPB;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-#pragma unroll
-        for (int u = 0; u < kPB; u += 4) {
-            const float4 gv = *reinterpret_cast<const float4*>(gr + u);
-            g0 = fmaf(gv.x, beta[u], g0);
-            g1 = fmaf(gv.y, beta[u + 1], g1);
-            g2 = fmaf(gv.z, beta[u + 2], g2);
-            g3 = fmaf(gv.w, beta[u + 3], g3);
-        }
-        const float gj = (g0 + g1) + (g2 + g3);
-        if (lane == m) {
-#pragma unroll
-            for (int u = 0; u < kPB; ++u) s.cb[u] = beta[u];
-        }
-        __syncwarp();
-        // gamma_m = 1 + sum_u G[m][u] beta[u][m]: lane u forms its term exactly as hi + lo
-        const float bu = s.cb[lane];
-        const float gh = gr[lane];
-        float hi = __fmul_rn(gh, bu);
-        float lo = __fmaf_rn(gh, bu, -hi);
-        lo = __fmaf_rn(s.Gl[m * kPB + lane], bu, lo);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            float t, e;
-            two_sum(hi, h2, t, e);
-            hi = t;
-            lo = __fadd_rn(__fadd_rn(lo, l2), e);
-        }
-        float g_hi, e1;
-        two_sum(1.f, hi, g_hi, e1);
-        float g_lo = __fadd_rn(lo, e1);
-        const float tmp = __fadd_rn(g_hi, g_lo);            // renormalise (|g_lo| << |g_hi|)
-        g_lo = __fsub_rn(g_lo, __fsub_rn(tmp, g_hi));
-        g_hi = tmp;
-        const float ginv = 1.0f / g_hi;
-        if (lane == m) ghi_l = g_hi, glo_l = g_lo, ginv_l = ginv;
-        // B[:,m] = beta_m / gamma_m, kept transposed
-        s.Bt[m * kPB + lane] = bu * ginv;
-        __syncwarp();
-        if (lane > m && lane < bp) {
-            const float* bm = s.Bt + m * kPB;
-#pragma unroll
-            for (int u = 0; u < kPB; u += 4) {
-                const float4 bv = *reinterpret_cast<const float4*>(bm + u);
-                beta[u] = fmaf(-bv.x, gj, beta[u]);
-                beta[u + 1] = fmaf(-bv.y, gj, beta[u + 1]);
-                beta[u + 2] = fmaf(-bv.z, gj, beta[u + 2]);
-                beta[u + 3] = fmaf(-bv.w, gj, beta[u + 3]);
-            }
-        }
-        __syncwarp();
-    }
-    if (lane < bp) {
-        s.gam[lane] = (double)ghi_l + (double)glo_l;
-        // final beta_l (= gamma_l B[:,l]) for the panel's own columns; B[:,l] = beta_l / gamma_l
-#pragma unroll
-        for (int u = 0; u < kPB; ++u) s.Bf[u * kPB + lane] = beta[u];
-        // L[m][l] = sum_u G[m][u] B[u][l] for m > l (lane l)
-        float bl[kPB];
-#pragma unroll
-        for (int u = 0; u < kPB; ++u) bl[u] = beta[u] * ginv_l;
-        for (int m = 0; m < bp; ++m) {
-            float v = 0.f;
-            if (m > lane) {
-                const float* gr = s.Gh + m * kPB;
-#pragma unroll
-                for (int u = 0; u < kPB; u += 4) {
-                    const float4 gv = *reinterpret_cast<const float4*>(gr + u);
-                    v = fmaf(gv.x, bl[u], v);
-                    v = fmaf(gv.y, bl[u + 1], v);
-                    v = fmaf(gv.z, bl[u + 2], v);
-                    v = fmaf(gv.w, bl[u + 3], v);
-                }
-            }
-            s.Lt[lane * kPB + m] = v;
-        }
-    }
-    __syncwarp();
-    panel_w(s, bp);
 }
 
 // Cross-CTA sum of the partial dots in a fixed order: each CTA owns a slice of the
@@ -314,13 +192,31 @@ __device__ __forceinline__ void writeback_tile(const float* xs, int ncl, int64_t
 // reads these rows of U_P.
 __device__ __forceinline__ void materialize_tile(const PanelArgs& a, const PanelSmem& s, const float* ups, int k0,
                                                  int bp, int64_t row0, int nr) {
-    static_assert(RT == 64, "row index mapping");
-    for (int e = threadIdx.x; e < bp * RT; e += kPT) {
-        const int m = e >> 6, j = e & 63;
-        if (j >= nr) continue;
-        float v = 0.f;
-        for (int u = 0; u <= m; ++u) v = fmaf(ups[u * RT + j], s.Bf[u * kPB + m], v);
-        col_ptr(a, k0 + m)[row0 + j] = v;
+    // thread: rows r4..r4+3, levels m and m + 16; beta[u][m] = 0 for u > m, so the sum runs
+    // over every u < bp in the same order as the triangular one
+    static_assert(RT == 64 && kPT == 256 && kPB == 32, "thread mapping");
+    const int r4 = (threadIdx.x & 15) * 4, mg = threadIdx.x >> 4;
+    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int u = 0; u < bp; ++u) {
+        const float4 x = *reinterpret_cast<const float4*>(&ups[u * RT + r4]);
+        const float b0 = s.Bf[u * kPB + mg], b1 = s.Bf[u * kPB + mg + 16];
+        acc0[0] = fmaf(x.x, b0, acc0[0]), acc0[1] = fmaf(x.y, b0, acc0[1]);
+        acc0[2] = fmaf(x.z, b0, acc0[2]), acc0[3] = fmaf(x.w, b0, acc0[3]);
+        acc1[0] = fmaf(x.x, b1, acc1[0]), acc1[1] = fmaf(x.y, b1, acc1[1]);
+        acc1[2] = fmaf(x.z, b1, acc1[2]), acc1[3] = fmaf(x.w, b1, acc1[3]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int m = mg + 16 * h;
+        if (m >= bp) continue;
+        const float* v = h ? acc1 : acc0;
+        float* dst = s.pu[m] + row0 + r4;
+        if (r4 + 4 <= nr && ((uintptr_t)dst & 15) == 0) {
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            for (int q = 0; q < 4; ++q)
+                if (r4 + q < nr) dst[q] = v[q];
+        }
     }
 }
 
@@ -375,14 +271,27 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
         };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
         auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
+        if (tid < CT) {
+            const int c = tid < ncl ? tid : 0;   // a valid address for zero-byte copies
+            s.psrc[tid] = scol(c);
+            s.pdst[tid] = xcol(c);
+        } else if (tid < CT + kPB) {
+            const int t = tid - CT;
+            s.pu[t] = ucol(t < bp ? t : 0);
+            s.pv[t] = vcol(t < nb ? t : 0);
+        }
+        auto psrc = [&](int c) { return s.psrc[c]; };
+        auto pdst = [&](int c) { return s.pdst[c]; };
+        auto pu = [&](int t) { return s.pu[t]; };
+        auto pv = [&](int t) { return s.pv[t]; };
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
             float* xs = s.Xs + buf * CT * XLD;
-            stage_cols<VEC>(xs, XLD, CT, ncl, row0, nr, scol);
-            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
-            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
+            stage_cols<VEC>(xs, XLD, CT, ncl, row0, nr, psrc);
+            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, pu);
+            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, pv);
             cp_async_commit();
         };
         __syncthreads();
@@ -404,7 +313,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
             if (step1) {
                 scale_tile(xs, r, r0 + rr, nr);
                 __syncthreads();
-                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
             }
             if (bp > 0) {
                 // GEMM1: rows 4 ty.., columns tx + 16 q
@@ -429,7 +338,7 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
                     *reinterpret_cast<float4*>(&xs[(tx + 16 * q) * XLD + ty * 4]) =
                         make_float4(x[0][q], x[1][q], x[2][q], x[3][q]);
                 __syncthreads();
-                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
                 if ((opts & kMaterialize) && c0 + CT >= ncols) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
             }
             if (nb > 0 && tq * 4 < nb) {
@@ -593,13 +502,26 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
         };
         auto ucol = [&](int t) { return col_ptr(a, k0 + t); };
         auto vcol = [&](int t) { return V + (int64_t)(kv + t) * a.ldv; };
+        if (tid < CT) {
+            const int c = tid < ncl ? tid : 0;   // a valid address for zero-byte copies
+            s.psrc[tid] = scol(c);
+            s.pdst[tid] = xcol(c);
+        } else if (tid < CT + kPB) {
+            const int t = tid - CT;
+            s.pu[t] = ucol(t < bp ? t : 0);
+            s.pv[t] = vcol(t < nb ? t : 0);
+        }
+        auto psrc = [&](int c) { return s.psrc[c]; };
+        auto pdst = [&](int c) { return s.pdst[c]; };
+        auto pu = [&](int t) { return s.pu[t]; };
+        auto pv = [&](int t) { return s.pv[t]; };
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
-            stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, scol);
-            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, ucol);
-            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, vcol);
+            stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, psrc);
+            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, pu);
+            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, pv);
             cp_async_commit();
         };
         __syncthreads();
@@ -691,10 +613,10 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                         if (SPLIT) s.Xl[col * HP + row] = Tc<PREC>::hi(v - Tc<PREC>::back(hv));
                     }
                 __syncthreads();
-                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+                writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
                 if ((opts & kMaterialize) && c0 + CT >= ncols) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
             }
-            if (step1) writeback_tile<VEC>(xs, ncl, r0 + rr, nr, xcol);
+            if (step1) writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
             if (nb > 0) {
                 // GEMM2: warp -> columns warp*8.. (one n-tile), t = 0..31 (two m-tiles), K = 64 rows
 #pragma unroll
@@ -812,12 +734,19 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     s.UPs = s.Xs + 2 * CT * XLD;
     s.VNs = s.UPs + 2 * kPB * RT;
     s.flag = reinterpret_cast<int*>(s.VNs + 2 * kPB * RT + kScratch);
+    {
+        void** tab = reinterpret_cast<void**>(s.flag + 4);
+        s.psrc = static_cast<const float**>(static_cast<void*>(tab));
+        s.pdst = reinterpret_cast<float**>(tab + CT);
+        s.pu = reinterpret_cast<float**>(tab + 2 * CT);
+        s.pv = static_cast<const float**>(static_cast<void*>(tab + 2 * CT + kPB));
+    }
     s.Gh = s.Xs;
     s.Gl = s.Gh + kPB * kPB;
     s.Bt = s.Gl + kPB * kPB;
     s.cb = s.Bt + kPB * kPB;
     {
-        unsigned short* h = reinterpret_cast<unsigned short*>(s.flag + 4);
+        unsigned short* h = reinterpret_cast<unsigned short*>(reinterpret_cast<void**>(s.flag + 4) + 2 * CT + 2 * kPB);
         s.Uh = h; h += kPB * HP;
         s.Ul = h; h += kPB * HP;
         s.Wh = h; h += CT * WPT;
@@ -904,7 +833,8 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
 
 size_t panel_smem(int prec) {
     const size_t base = sizeof(double) * (kPB + 32) +
-                        sizeof(float) * (3 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16;
+                        sizeof(float) * (3 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16 +
+                        sizeof(void*) * (2 * CT + 2 * kPB);
     const size_t tc = sizeof(unsigned short) * 2 * (2 * kPB * HP + CT * WPT + CT * HP);
     return base + (prec ? tc : 0);
 }
