@@ -62,37 +62,49 @@ __device__ __forceinline__ int col_of(int a, int N, int k1) {
 }
 
 // Step 1 into the row-major iterate: X[j][c] = V[j,c]/r_j, X[j][N+c] = D[j,c]/r_j, Vr[j][c] = V[j,c].
-// 32 x 32 tiles are read coalesced over rows and written coalesced over columns.
-__device__ void load_problem(const BatchDesc& d, const float* __restrict__ in, float* X, float* Vr, float* tile,
+// 32 x 32 tiles, one per warp at a time in the warp's own shared-memory tiles (XOR-
+// swizzled, 2 x 4 KB per warp): read coalesced over rows, written coalesced over
+// columns, no CTA barrier in the loop.
+__device__ void load_problem(const BatchDesc& d, const float* __restrict__ in, float* X, float* Vr, float* wtiles,
                              Control* ctl) {
-    float* tile2 = tile + 32 * 33;
     const int n = d.nobs, N = d.nens, ldX = d.ldX, ldVr = d.ldVr;
     const float* r = in + d.r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ncb = (2 * N + 31) / 32;
-    for (int j0 = 0; j0 < n; j0 += 32) {
-        for (int cb = 0; cb < ncb; ++cb) {
-            __syncthreads();
-            // read 32 rows x 32 columns (column-major source, coalesced over rows)
-            for (int cc = warp; cc < 32; cc += kBT / 32) {
-                const int c = cb * 32 + cc, j = j0 + lane;
-                float v = 0.f, src = 0.f;
-                if (c < 2 * N && j < n) {
-                    const float rj = r[j];
-                    src = c < N ? in[d.V + (int64_t)c * d.ldv + j] : in[d.D + (int64_t)(c - N) * d.ldd + j];
-                    if (!(rj > 0.f) || !isfinite(rj)) set_status(ctl, kErrNumeric);
-                    v = src / rj;
-                }
-                tile[cc * 33 + lane] = v;
-                tile2[cc * 33 + lane] = src;
+    float* t1 = wtiles + warp * (2 * 32 * 32);
+    float* t2 = t1 + 32 * 32;
+    const int ncb = (2 * N + 31) / 32, njb = (n + 31) / 32;
+    __syncthreads();
+    for (int tt = warp; tt < njb * ncb; tt += kBT / 32) {
+        const int j0 = (tt / ncb) * 32, cb = tt % ncb;
+        const int j = j0 + lane;
+        const float rj = j < n ? r[j] : 1.f;
+        if (j < n && (!(rj > 0.f) || !isfinite(rj))) set_status(ctl, kErrNumeric);
+#pragma unroll
+        for (int h = 0; h < 32; h += 16) {     // 16 columns in flight per lane
+            float src[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int c = cb * 32 + h + q;
+                src[q] = (c < 2 * N && j < n)
+                             ? (c < N ? in[d.V + (int64_t)c * d.ldv + j] : in[d.D + (int64_t)(c - N) * d.ldd + j])
+                             : 0.f;
             }
-            __syncthreads();
-            for (int jj = warp; jj < 32; jj += kBT / 32) {
-                const int j = j0 + jj, c = cb * 32 + lane;
-                if (j < n && c < 2 * N) X[(int64_t)j * ldX + c] = tile[lane * 33 + jj];
-                if (j < n && c < N) Vr[(int64_t)j * ldVr + c] = tile2[lane * 33 + jj];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int cc = h + q;
+                t1[cc * 32 + (lane ^ cc)] = src[q] / rj;
+                t2[cc * 32 + (lane ^ cc)] = src[q];
             }
         }
+        __syncwarp();
+        const int c = cb * 32 + lane;
+        for (int jj = 0; jj < 32; ++jj) {
+            const int jr = j0 + jj;
+            if (jr >= n) break;
+            if (c < 2 * N) X[(int64_t)jr * ldX + c] = t1[lane * 32 + (jj ^ lane)];
+            if (c < N) Vr[(int64_t)jr * ldVr + c] = t2[lane * 32 + (jj ^ lane)];
+        }
+        __syncwarp();
     }
     __syncthreads();
 }
@@ -111,9 +123,9 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
     const int a = active ? t % ncols : 0;
     const int g = active ? t / ncols : 0;
     float w[B];
-    float acc[B], outer[B];
+    float acc[B];      // running dots; folded every 64 rows into this thread's row of s.apart
 #pragma unroll
-    for (int q = 0; q < B; ++q) acc[q] = 0.f, outer[q] = 0.f, w[q] = 0.f;
+    for (int q = 0; q < B; ++q) acc[q] = 0.f, w[q] = 0.f;
     if (update && active) {
         // w = W a_col for this column (a_col = dots of the panel's V with this column, index a + bp)
 #pragma unroll
@@ -125,6 +137,8 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
         }
     }
     __syncthreads();   // s.A is rewritten below
+    if (active)
+        for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] = 0.f;
     // rows in blocks of 32: the panel rows of U_P and V_{P'} are staged in shared memory
     // (zero beyond bp / nb) and read as broadcasts, four per 16-byte load
     float* Us = s.tile;                 // [32][B]
@@ -141,9 +155,19 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
         __syncthreads();
         if (!active) continue;
         const int jend = min(32, n - j0);
-        for (int jj = g; jj < jend; jj += G) {
+        for (int jq = g; jq < jend; jq += 4 * G) {
+          float xq[4];   // the next four rows of this column, loaded ahead of their use
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+              const int jj = jq + u * G;
+              xq[u] = jj < jend ? X[(int64_t)(j0 + jj) * ldX + col] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int jj = jq + u * G;
+            if (jj >= jend) break;
             const int64_t j = j0 + jj;
-            float x = X[j * ldX + col];
+            float x = xq[u];
             if (update) {
 #pragma unroll
                 for (int q = 0; q < B; q += (B >= 4 ? 4 : 1)) {
@@ -175,14 +199,15 @@ __device__ void sweep(const BatchDesc& d, float* X, const float* Vr, const SmemB
                 if (++cnt == 64) {
                     cnt = 0;
 #pragma unroll
-                    for (int q = 0; q < B; ++q) outer[q] += acc[q], acc[q] = 0.f;
+                    for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] += acc[q], acc[q] = 0.f;
                 }
             }
+          }
         }
     }
     if (active) {
 #pragma unroll
-        for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] = outer[q] + acc[q];
+        for (int q = 0; q < B; ++q) s.apart[t * kBmax + q] += acc[q];
     }
     __syncthreads();
     if (nb > 0) {
@@ -252,66 +277,103 @@ __device__ void panel_final_columns(const BatchDesc& d, float* X, const SmemB& s
 
 // M = V^T Z / sqrt(N-1) and Z out (column-major).  256 threads, thread -> (k, i) blocks.
 __device__ void finish_problem(const BatchDesc& d, float* __restrict__ out, const float* X, const float* Vr,
-                               float* tile, const float* Ch, float* ws_q) {
+                               float* tile, float* stage, const float* Ch, float* ws_q) {
     const int n = d.nobs, N = d.nens, ldX = d.ldX, ldVr = d.ldVr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // Z out: transpose X[:, N..2N) -> Z (column-major)
     if (d.Z >= 0) {
-        const int ncb = (N + 31) / 32;
-        for (int j0 = 0; j0 < n; j0 += 32) {
-            for (int cb = 0; cb < ncb; ++cb) {
-                __syncthreads();
-                for (int jj = warp; jj < 32; jj += kBT / 32) {
-                    const int j = j0 + jj, c = cb * 32 + lane;
-                    tile[jj * 33 + lane] = (j < n && c < N) ? X[(int64_t)j * ldX + N + c] : 0.f;
+        // one 32 x 32 tile per warp at a time in the warp's own shared-memory tile
+        float* wt = stage + warp * (32 * 32);   // XOR-swizzled 32 x 32 tile
+        const int ncb = (N + 31) / 32, njb = (n + 31) / 32;
+        __syncthreads();
+        for (int tt = warp; tt < njb * ncb; tt += kBT / 32) {
+            const int j0 = (tt / ncb) * 32, cb = tt % ncb;
+            const int c = cb * 32 + lane;
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {
+                float row[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int j = j0 + h + q;
+                    row[q] = (j < n && c < N) ? X[(int64_t)j * ldX + N + c] : 0.f;
                 }
-                __syncthreads();
-                for (int cc = warp; cc < 32; cc += kBT / 32) {
-                    const int c = cb * 32 + cc, j = j0 + lane;
-                    if (j < n && c < N) out[d.Z + (int64_t)c * d.ldz + j] = tile[lane * 33 + cc];
-                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) wt[(h + q) * 32 + (lane ^ (h + q))] = row[q];
             }
+            __syncwarp();
+            const int j = j0 + lane;
+            for (int cc = 0; cc < 32; ++cc) {
+                const int cz = cb * 32 + cc;
+                if (cz >= N) break;
+                if (j < n) out[d.Z + (int64_t)cz * d.ldz + j] = wt[lane * 32 + (cc ^ lane)];
+            }
+            __syncwarp();
         }
+        __syncthreads();
     }
     if (d.M >= 0 && N >= 2) {
         // Q_km = v_k^T u_m (k < m) in 4 x 4 blocks (N % 4 == 0), FP32 products folded into FP64
         // every 32 rows; then M = (I - triu(Q,1)) chat / sqrt(N-1).
         float* Qw = ws_q;
         const int nb4 = N / 4;
-        for (int blk = threadIdx.x; blk < nb4 * nb4; blk += kBT) {
-            const int kb = blk % nb4, mb = blk / nb4;
-            if (kb > mb) continue;
+        const int nblk = nb4 * (nb4 + 1) / 2;            // upper blocks kb <= mb
+        float* Vt = stage;                               // [32][N] rows of V
+        float* Ut = stage + 32 * N;                      // [32][N] rows of the final U
+        for (int b0 = 0; b0 < nblk; b0 += kBT) {
+            int kb = 0, mb = 0;
+            const int blk = b0 + threadIdx.x;
+            if (blk < nblk) {                            // blk -> (kb, mb), kb <= mb, row by row
+                int t = blk;
+                while (t >= nb4 - kb) t -= nb4 - kb, ++kb;
+                mb = kb + t;
+            }
             float acc[16];
             double accd[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) acc[q] = 0.f, accd[q] = 0.0;
-            for (int j = 0; j < n; ++j) {
-                const float4 v = *reinterpret_cast<const float4*>(Vr + (int64_t)j * ldVr + 4 * kb);
-                const float4 u = *reinterpret_cast<const float4*>(X + (int64_t)j * ldX + 4 * mb);
-                const float vv[4] = {v.x, v.y, v.z, v.w};
-                const float uu[4] = {u.x, u.y, u.z, u.w};
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < 32 * (N / 4); e += kBT) {
+                    const int jj = e / (N / 4), c4 = (e % (N / 4)) * 4, j = j0 + jj;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f), u = v;
+                    if (j < n) {
+                        v = *reinterpret_cast<const float4*>(Vr + (int64_t)j * ldVr + c4);
+                        u = *reinterpret_cast<const float4*>(X + (int64_t)j * ldX + c4);
+                    }
+                    *reinterpret_cast<float4*>(Vt + jj * N + c4) = v;
+                    *reinterpret_cast<float4*>(Ut + jj * N + c4) = u;
+                }
+                __syncthreads();
+                if (blk < nblk) {
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const float4 v = *reinterpret_cast<const float4*>(Vt + jj * N + 4 * kb);
+                        const float4 u = *reinterpret_cast<const float4*>(Ut + jj * N + 4 * mb);
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+                        const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int p = 0; p < 4; ++p) acc[q * 4 + p] = fmaf(vv[q], uu[p], acc[q * 4 + p]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) accd[q] += (double)acc[q], acc[q] = 0.f;   // every 32 rows
+                }
+            }
+            if (blk < nblk) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) acc[q * 4 + p] = fmaf(vv[q], uu[p], acc[q * 4 + p]);
-                if ((j & 31) == 31) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) accd[q] += (double)acc[q], acc[q] = 0.f;
-                }
+                    for (int p = 0; p < 4; ++p)
+                        Qw[(int64_t)(4 * kb + q) * N + 4 * mb + p] = (float)accd[q * 4 + p];
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    Qw[(int64_t)(4 * kb + q) * N + 4 * mb + p] = (float)(accd[q * 4 + p] + (double)acc[q * 4 + p]);
         }
         __syncthreads();
         const float scale = (float)(1.0 / sqrt((double)(N - 1)));
         for (int e = threadIdx.x; e < N * N; e += kBT) {
-            const int k = e % N, i = e / N;
+            const int k = e / N, i = e % N;   // a warp shares k (Q row broadcast), chat rows coalesced
             float v = Ch[(int64_t)k * N + i];
             for (int m = k + 1; m < N; ++m) v = fmaf(-Qw[(int64_t)k * N + m], Ch[(int64_t)m * N + i], v);
-            out[d.M + e] = v * scale;
+            out[d.M + k + (int64_t)i * N] = v * scale;
         }
     }
     __syncthreads();
@@ -324,7 +386,7 @@ __device__ void solve_problem(const BatchDesc& d, const float* in, float* out, f
     float* Vr = ws + d.Vr;
     float* Ch = ws + d.Ch;
     const int N = d.nens;
-    load_problem(d, in, X, Vr, s.tile, ctl);
+    load_problem(d, in, X, Vr, s.apart, ctl);
     // initial dots of panel 0 with every column
     int bp = B < N ? B : N;
     sweep<B>(d, X, Vr, s, 0, 0, 0, bp, false);
@@ -337,7 +399,7 @@ __device__ void solve_problem(const BatchDesc& d, const float* in, float* out, f
         sweep<B>(d, X, Vr, s, k0, bp, k1, nb, true);
         panel_final_columns(d, X, s, k0, bp);
     }
-    finish_problem(d, out, X, Vr, s.tile, Ch, ws + d.Qw);
+    finish_problem(d, out, X, Vr, s.tile, s.apart, Ch, ws + d.Qw);
 }
 
 __global__ void __launch_bounds__(kBT, 2) ism_batch_kernel(const BatchDesc* __restrict__ desc,
