@@ -280,21 +280,31 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
         const int quarter = warp & 3, half = warp >> 2;
         const int ngroups = nb / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
         int64_t t = 0;
+        auto load_xb = [&](int64_t i, int gq, float* xb) {
+            const int e0 = yb * nb + gq * 16;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                xb[q] = (i < p.nstate && e0 + q < p.nens) ? p.XB[(int64_t)(e0 + q) * p.ldb + i] : 0.f;
+        };
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
             const int b = (int)(t & 1);
+            const int64_t i = tile * XM + quarter * 32 + lane;
+            // X_B does not depend on the MMAs: the first group's loads are issued before the wait,
+            // and each later group's one group ahead of its use
+            float xnext[16];
+            if (g0 < g1) load_xb(i, g0, xnext);
             if (!mbar_wait(&sh->acc_full[b], (unsigned)((t >> 1) & 1), sh, p.ctl, p.timeout_ns)) break;
             tc_fence_after();
-            const int64_t i = tile * XM + quarter * 32 + lane;
             const unsigned row_addr = tbase + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * nb);
             for (int gq = g0; gq < g1; ++gq) {
-                const int e0 = yb * nb + gq * 16;
                 float xb[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    xb[q] = (i < p.nstate && e0 + q < p.nens) ? p.XB[(int64_t)(e0 + q) * p.ldb + i] : 0.f;
+                for (int q = 0; q < 16; ++q) xb[q] = xnext[q];
+                if (gq + 1 < g1) load_xb(i, gq + 1, xnext);
                 unsigned acc[16];
                 tmem_ld16(row_addr + gq * 16, acc);
                 tmem_wait_ld();
+                const int e0 = yb * nb + gq * 16;
                 if (i < p.nstate) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
