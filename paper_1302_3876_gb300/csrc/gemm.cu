@@ -38,10 +38,12 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) gram_upper_kernel(int64_t nrows, int n, const T* __restrict__ A, int64_t lda,
                                                          const T* __restrict__ B, int64_t ldb, int64_t rows_per_split,
                                                          double* __restrict__ Qpart, int full) {
-    // two stages of SR rows x 64 columns of A and B, [column][row] (odd row pitch: conflict-free)
+    // two stages of SR rows x 64 columns of A and B, [row][column] (pitch GT + 4) so that a
+    // thread's four columns are one 16-byte load
     constexpr int SR = sizeof(T) == 8 ? GR / 2 : GR;
-    __shared__ T As[2][GT][SR + 1];
-    __shared__ T Bs[2][GT][SR + 1];
+    constexpr int CP = GT + 4;
+    __shared__ __align__(16) T As[2][SR][CP];
+    __shared__ __align__(16) T Bs[2][SR][CP];
     // map blockIdx.x to a tile: every (kb, mb) when full, else the upper tiles (kb <= mb)
     const int nt = (n + GT - 1) / GT;
     int kb = 0, mb = 0;
@@ -73,8 +75,8 @@ __global__ void __launch_bounds__(256, 2) gram_upper_kernel(int64_t nrows, int n
         for (int c = tid / SR; c < GT; c += 256 / SR) {
             const int ka = kb * GT + c, mbc = mb * GT + c;
             const bool va = j < j1 && ka < n, vb = j < j1 && mbc < n;
-            cp_async_elem(&As[buf][c][lr], va ? A + (int64_t)ka * lda + j : A, va);
-            cp_async_elem(&Bs[buf][c][lr], vb ? B + (int64_t)mbc * ldb + j : B, vb);
+            cp_async_elem(&As[buf][lr][c], va ? A + (int64_t)ka * lda + j : A, va);
+            cp_async_elem(&Bs[buf][lr][c], vb ? B + (int64_t)mbc * ldb + j : B, vb);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -93,9 +95,9 @@ __global__ void __launch_bounds__(256, 2) gram_upper_kernel(int64_t nrows, int n
         for (int j = 0; j < SR; ++j) {
             T a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[buf][ty * 4 + i][j];
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][j][ty * 4 + i];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = Bs[buf][tx * 4 + q][j];
+            for (int q = 0; q < 4; ++q) b[q] = Bs[buf][j][tx * 4 + q];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
