@@ -271,6 +271,7 @@ def run_ours(args):
     XA = torch.empty_like(dX)
     M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
     mode = {"panel32": enkf.ENKF_PANEL_FP32, "bf16": enkf.ENKF_PANEL_BF16, "fp16": enkf.ENKF_PANEL_FP16,
+            "bf16x3": enkf.ENKF_PANEL_BF16X3,
             "fp32": enkf.ENKF_FP32}[args.mode]
     plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode != "fp32" else 0,
                      flags=enkf.ENKF_FLAG_REFINE if args.refine else 0, device=dev)
@@ -373,13 +374,13 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_stream.cu"),
                                                "ism_levels_large_single_fp32.md")}
-    elif args.mode in ("bf16", "fp16"):
+    elif args.mode in ("bf16", "fp16", "bf16x3"):
         f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
         pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
         achieved = pb / (lv_avg / 1e3) / 1e9
-        mult = 3 if args.mode == "bf16" else 1            # split operands: three tensor products
+        mult = {"bf16": 3, "fp16": 1, "bf16x3": 6}[args.mode]   # tensor products per operand pair
         bf16_peak = read_bf16_peak()
-        roofline = {"kernel": "ism_panel_kernel<%d>" % (1 if args.mode == "bf16" else 2), "bound": "hbm",
+        roofline = {"kernel": "ism_panel_kernel<%d>" % {"bf16": 1, "fp16": 2, "bf16x3": 3}[args.mode], "bound": "hbm",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)", "algorithmic_bytes_per_launch": pb,
                     "avg_launch_ms": lv_avg,
@@ -412,6 +413,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "nstate": NSTATE, "nobs": NOBS, "nens": NENS,
                    "path": {"panel32": "panel form on FP32 CUDA cores, b=%d (FP64 gamma)" % args.panel_b,
                             "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)" % args.panel_b,
+                            "bf16x3": "panel form on tensor cores, BF16 operands split in three, b=%d (FP64 gamma)"
+                                      % args.panel_b,
                             "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)" % args.panel_b,
                             "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}[args.mode],
                    "refine": bool(args.refine),
@@ -616,9 +619,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["panel32", "bf16", "fp16", "fp32"], default="panel32",
+    ap.add_argument("--mode", choices=["panel32", "bf16", "fp16", "bf16x3", "fp32"], default="panel32",
                     help="headline path: panel form on FP32 CUDA cores (panel32), on tensor cores with split BF16 "
-                         "(bf16) or FP16 (fp16) operands, or the FP32 level-streaming path (fp32)")
+                         "(bf16), three-piece BF16 (bf16x3) or FP16 (fp16) operands, or the FP32 level-streaming "
+                         "path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
     ap.add_argument("--refine", action="store_true", help="one step of iterative refinement (panel modes)")
     ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle"],

@@ -73,7 +73,10 @@ typedef enum {
                              (x = hi + lo, three products), FP32 storage/accumulation, FP64 denominators */
     ENKF_PANEL_FP16 = 3,  /* panel form, tensor-core trailing updates and dots in one FP16 product,
                              FP32 storage/accumulation, FP64 denominators */
-    ENKF_PANEL_FP32 = 4   /* panel form on FP32 CUDA cores (b levels per pass), FP64 denominators */
+    ENKF_PANEL_FP32 = 4,  /* panel form on FP32 CUDA cores (b levels per pass), FP64 denominators */
+    ENKF_PANEL_BF16X3 = 5 /* panel form, tensor-core trailing updates and dots with BF16 operands split
+                             in three (x = hi + mid + lo, six products: operands kept to ~2^-25),
+                             FP32 storage/accumulation, FP64 denominators */
 } enkf_mode;
 
 /* Plan flags. */

@@ -113,7 +113,8 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     if (nens > 1024) return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: nens %d > 1024", nens);
     if (nobs > ((int64_t)1 << 40) || nstate > ((int64_t)1 << 40))
         return fail(ENKF_ERR_SHAPE, "enkf_ism_plan: size too large");
-    const bool panel = (mode == ENKF_PANEL_FP32 || mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16);
+    const bool panel = (mode == ENKF_PANEL_FP32 || mode == ENKF_PANEL_BF16 || mode == ENKF_PANEL_FP16 ||
+                        mode == ENKF_PANEL_BF16X3);
     if (mode != ENKF_FP64 && mode != ENKF_FP32 && !panel) return fail(ENKF_ERR_ARG, "enkf_ism_plan: bad mode %d", mode);
     if (panel && (panel_b < 0 || panel_b > panel_max_b()))
         return fail(ENKF_ERR_ARG, "enkf_ism_plan: panel_b %d out of [1, %d]", panel_b, panel_max_b());
@@ -132,7 +133,10 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) {
         if (panel) {
-            const int prec = mode == ENKF_PANEL_BF16 ? 1 : mode == ENKF_PANEL_FP16 ? 2 : 0;
+            const int prec = mode == ENKF_PANEL_BF16     ? 1
+                             : mode == ENKF_PANEL_FP16   ? 2
+                             : mode == ENKF_PANEL_BF16X3 ? 3
+                                                         : 0;
             e = panel_plan(nobs, nens, p->panel_b, prec, &p->P);
             p->L.grid = p->P.grid;
         } else {
@@ -320,7 +324,8 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
     int slot = prof_begin(p, 1, s);
     PanelArgs panel_args;
-    if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16) {
+    if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16 ||
+        p->mode == ENKF_PANEL_BF16X3) {
         PanelArgs pa;
         pa.nobs = p->nobs;
         pa.nens = p->nens;

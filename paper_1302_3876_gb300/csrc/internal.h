@@ -77,7 +77,7 @@ struct PanelLaunch {
     size_t smem;
     int rows_per_blk;
     int b;
-    int prec;                      // 0 FP32 CUDA cores, 1 BF16 split tensor cores, 2 FP16 tensor cores
+    int prec;                      // 0 FP32 CUDA cores; tensor cores: 1 BF16 x2 pieces, 2 FP16, 3 BF16 x3 pieces
     int64_t part_stride;
 };
 

@@ -61,10 +61,11 @@ struct PanelSmem {
     float** pu;           // [kPB]
     const float** pv;     // [kPB]
     // tensor-core variants: 16-bit operand tiles (hi, and lo for the split form)
-    unsigned short *Uh, *Ul;   // [kPB][HP]   -U_P, [t][row]
-    unsigned short *Wh, *Wl;   // [CT][WPT]   W',   [col][t]
-    unsigned short *Xh, *Xl;   // [CT][HP]    X,    [col][row]
-    unsigned short *Vh, *Vl;   // [kPB][HP]   V',   [t][row]
+    // (pieces: [0] = hi, [1] = the next 8 bits, [2] = the last 8 bits)
+    unsigned short* U3[3];     // [kPB][HP]   -U_P, [t][row]
+    unsigned short* W3[3];     // [CT][WPT]   W',   [col][t]
+    unsigned short* X3[3];     // [CT][HP]    X,    [col][row]
+    unsigned short* V3[3];     // [kPB][HP]   V',   [t][row]
 };
 constexpr int HP = RT + 8;     // 16-bit tile pitch along rows
 constexpr int WPT = kPB + 8;   // 16-bit tile pitch along t
@@ -389,9 +390,13 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core sweep (mma.sync m16n8k16, FP32 accumulation).  PREC 1: BF16 split
-// operands (x = hi + lo, three products hi*hi + hi*lo + lo*hi); PREC 2: FP16,
-// one product.  Same data flow as the FP32 sweep; the two GEMMs of a 64 x 64 tile:
+// Tensor-core sweep (mma.sync m16n8k16, FP32 accumulation).  Operands are split into
+// P 16-bit pieces x = x_0 + x_1 + ... and the products x_i y_j with i + j < P are
+// summed, smallest first:
+//   PREC 1  BF16, P = 2 (hi + lo, three products; operands kept to ~2^-17)
+//   PREC 2  FP16, P = 1 (one product)
+//   PREC 3  BF16, P = 3 (hi + mid + lo, six products; operands kept to ~2^-25, FP32-class)
+// Same data flow as the FP32 sweep; the two GEMMs of a 64 x 64 tile:
 //   GEMM1  X <- X + (-U_P) W'      (M = rows, N = columns, K = t), accumulators start at X
 //   GEMM2  A' += V'^T X_new        (M = t, N = columns, K = rows), accumulators persist
 // ---------------------------------------------------------------------------
@@ -399,7 +404,7 @@ template <int PREC>
 struct Tc;
 template <>
 struct Tc<1> {
-    static constexpr bool split = true;
+    static constexpr int pieces = 2;
     static __device__ __forceinline__ unsigned short hi(float x) { return __bfloat16_as_ushort(__float2bfloat16(x)); }
     static __device__ __forceinline__ float back(unsigned short h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
     static __device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
@@ -412,7 +417,7 @@ struct Tc<1> {
 };
 template <>
 struct Tc<2> {
-    static constexpr bool split = false;
+    static constexpr int pieces = 1;
     static __device__ __forceinline__ unsigned short hi(float x) { return __half_as_ushort(__float2half_rn(x)); }
     static __device__ __forceinline__ float back(unsigned short h) { return __half2float(__ushort_as_half(h)); }
     static __device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
@@ -422,6 +427,11 @@ struct Tc<2> {
             : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
     }
+};
+
+template <>
+struct Tc<3> : Tc<1> {
+    static constexpr int pieces = 3;
 };
 
 __device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
@@ -439,24 +449,53 @@ __device__ __forceinline__ void ldsm2(uint32_t* r, const void* p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
 }
 
-// hi (and lo) of 4 floats stored as 4 consecutive 16-bit values
+// The P pieces of x: each is the 16-bit rounding of what the previous ones leave
+// (the subtractions are exact in FP32).
 template <int PREC>
-__device__ __forceinline__ void put4(unsigned short* h, unsigned short* l, float4 v) {
-    const float f[4] = {v.x, v.y, v.z, v.w};
-    __align__(8) unsigned short hh[4], ll[4];
+__device__ __forceinline__ void split_pieces(float x, unsigned short* out) {
+    float rest = x;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        hh[q] = Tc<PREC>::hi(f[q]);
-        if (Tc<PREC>::split) ll[q] = Tc<PREC>::hi(f[q] - Tc<PREC>::back(hh[q]));
+    for (int p = 0; p < Tc<PREC>::pieces; ++p) {
+        out[p] = Tc<PREC>::hi(rest);
+        if (p + 1 < Tc<PREC>::pieces) rest = rest - Tc<PREC>::back(out[p]);
     }
-    *reinterpret_cast<uint2*>(h) = *reinterpret_cast<const uint2*>(hh);
-    if (Tc<PREC>::split) *reinterpret_cast<uint2*>(l) = *reinterpret_cast<const uint2*>(ll);
+}
+
+// The pieces of 4 floats stored as 4 consecutive 16-bit values in each piece array.
+template <int PREC>
+__device__ __forceinline__ void put4(unsigned short* d0, unsigned short* d1, unsigned short* d2, int off, float4 v) {
+    unsigned short x[3], y[3], z[3], w[3];
+    split_pieces<PREC>(v.x, x);
+    split_pieces<PREC>(v.y, y);
+    split_pieces<PREC>(v.z, z);
+    split_pieces<PREC>(v.w, w);
+    *reinterpret_cast<uint2*>(d0 + off) =
+        make_uint2((uint32_t)x[0] | ((uint32_t)y[0] << 16), (uint32_t)z[0] | ((uint32_t)w[0] << 16));
+    if (Tc<PREC>::pieces > 1)
+        *reinterpret_cast<uint2*>(d1 + off) =
+            make_uint2((uint32_t)x[1] | ((uint32_t)y[1] << 16), (uint32_t)z[1] | ((uint32_t)w[1] << 16));
+    if (Tc<PREC>::pieces > 2)
+        *reinterpret_cast<uint2*>(d2 + off) =
+            make_uint2((uint32_t)x[2] | ((uint32_t)y[2] << 16), (uint32_t)z[2] | ((uint32_t)w[2] << 16));
+}
+
+// d += sum over piece pairs (i, j), i + j < P, of a_i b_j, smallest terms first
+// (P = 2: a1 b0, a0 b1, a0 b0; P = 3: a2 b0, a1 b1, a0 b2, a1 b0, a0 b1, a0 b0).
+template <int PREC>
+__device__ __forceinline__ void mma_pieces(float* d, const uint32_t (&a)[Tc<PREC>::pieces][4],
+                                           const uint32_t (&b0)[Tc<PREC>::pieces],
+                                           const uint32_t (&b1)[Tc<PREC>::pieces]) {
+    constexpr int P = Tc<PREC>::pieces;
+#pragma unroll
+    for (int sum = P - 1; sum >= 0; --sum)
+#pragma unroll
+        for (int i = sum; i >= 0; --i) Tc<PREC>::mma(d, a[i], b0[sum - i], b1[sum - i]);
 }
 
 template <bool VEC, int PREC>
 __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int64_t nrows, int k0, int bp, int ku,
                          int kv, int nb, int aoff, int opts) {
-    constexpr bool SPLIT = Tc<PREC>::split;
+    constexpr int P = Tc<PREC>::pieces;
     const int N = a.nens;
     const int k1 = ku;
     const int ncols = (N - k1) + N;
@@ -484,9 +523,10 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                 float v = 0.f;
                 if (t < bp)
                     for (int u = 0; u < bp; ++u) v = fmaf(s.W[t * kPB + u], As[u * CT + c], v);
-                const unsigned short h = Tc<PREC>::hi(v);
-                s.Wh[c * WPT + t] = h;
-                if (SPLIT) s.Wl[c * WPT + t] = Tc<PREC>::hi(v - Tc<PREC>::back(h));
+                unsigned short pc[3];
+                split_pieces<PREC>(v, pc);
+#pragma unroll
+                for (int q = 0; q < P; ++q) s.W3[q][c * WPT + t] = pc[q];
             }
         }
         float acc2[2][4];
@@ -550,53 +590,51 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                 if (bp > 0) {
                     float4 u = t < bp ? *reinterpret_cast<const float4*>(&ups[t * RT + r4]) : make_float4(0, 0, 0, 0);
                     u.x = -u.x, u.y = -u.y, u.z = -u.z, u.w = -u.w;
-                    put4<PREC>(s.Uh + t * HP + r4, s.Ul + t * HP + r4, u);
+                    put4<PREC>(s.U3[0], s.U3[1], s.U3[2], t * HP + r4, u);
                 }
                 if (nb > 0) {
                     const float4 v = t < nb ? *reinterpret_cast<const float4*>(&vns[t * RT + r4]) : make_float4(0, 0, 0, 0);
-                    put4<PREC>(s.Vh + t * HP + r4, s.Vl + t * HP + r4, v);
+                    put4<PREC>(s.V3[0], s.V3[1], s.V3[2], t * HP + r4, v);
                 }
             }
             if (bp == 0) {
                 for (int e = tid; e < CT * (RT / 4); e += kPT) {
                     const int c = e >> 4, r4 = (e & 15) * 4;
-                    put4<PREC>(s.Xh + c * HP + r4, s.Xl + c * HP + r4, *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
+                    put4<PREC>(s.X3[0], s.X3[1], s.X3[2], c * HP + r4,
+                               *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
                 }
             }
             __syncthreads();
             if (bp > 0) {
                 // GEMM1: warp -> rows mt*16.., columns nb0.. (4 n-tiles)
                 const int mt = warp & 3, nb0 = (warp >> 2) * 32;
+                // the update (-U_P W') accumulates from zero in the tensor core; X is added
+                // afterwards with an IEEE FP32 add (tensor-core accumulation is truncating, and
+                // its error would otherwise scale with |X| rather than with the update)
                 float acc1[4][4];
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int row = mt * 16 + (lane >> 2) + (h >> 1) * 8;
-                        const int col = nb0 + nt * 8 + (lane & 3) * 2 + (h & 1);
-                        acc1[nt][h] = xs[col * XLD + row];
-                    }
+                    for (int h = 0; h < 4; ++h) acc1[nt][h] = 0.f;
                 for (int kk = 0; kk < bp; kk += 16) {
-                    uint32_t ah[4], al[4];
+                    uint32_t af[P][4];
                     const int kr = kk + (j8 >> 1) * 8 + (lane & 7);
                     const int mr = mt * 16 + (j8 & 1) * 8;
-                    ldsm4t(ah, s.Uh + kr * HP + mr);
-                    if (SPLIT) ldsm4t(al, s.Ul + kr * HP + mr);
+#pragma unroll
+                    for (int q = 0; q < P; ++q) ldsm4t(af[q], s.U3[q] + kr * HP + mr);
 #pragma unroll
                     for (int np = 0; np < 2; ++np) {
                         const int nr2 = nb0 + np * 16 + (j8 >> 1) * 8 + (lane & 7);
                         const int kc = kk + (j8 & 1) * 8;
-                        uint32_t bh[4], bl[4];
-                        ldsm4(bh, s.Wh + nr2 * WPT + kc);
-                        if (SPLIT) ldsm4(bl, s.Wl + nr2 * WPT + kc);
+                        uint32_t bf[P][4];
+#pragma unroll
+                        for (int q = 0; q < P; ++q) ldsm4(bf[q], s.W3[q] + nr2 * WPT + kc);
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
-                            float* d = acc1[np * 2 + hh];
-                            if (SPLIT) {
-                                Tc<PREC>::mma(d, al, bh[2 * hh], bh[2 * hh + 1]);
-                                Tc<PREC>::mma(d, ah, bl[2 * hh], bl[2 * hh + 1]);
-                            }
-                            Tc<PREC>::mma(d, ah, bh[2 * hh], bh[2 * hh + 1]);
+                            uint32_t b0[P], b1[P];
+#pragma unroll
+                            for (int q = 0; q < P; ++q) b0[q] = bf[q][2 * hh], b1[q] = bf[q][2 * hh + 1];
+                            mma_pieces<PREC>(acc1[np * 2 + hh], af, b0, b1);
                         }
                     }
                 }
@@ -606,11 +644,12 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                     for (int h = 0; h < 4; ++h) {
                         const int row = mt * 16 + (lane >> 2) + (h >> 1) * 8;
                         const int col = nb0 + nt * 8 + (lane & 3) * 2 + (h & 1);
-                        const float v = acc1[nt][h];
+                        const float v = xs[col * XLD + row] + acc1[nt][h];
                         xs[col * XLD + row] = v;
-                        const unsigned short hv = Tc<PREC>::hi(v);
-                        s.Xh[col * HP + row] = hv;
-                        if (SPLIT) s.Xl[col * HP + row] = Tc<PREC>::hi(v - Tc<PREC>::back(hv));
+                        unsigned short pc[3];
+                        split_pieces<PREC>(v, pc);
+#pragma unroll
+                        for (int q = 0; q < P; ++q) s.X3[q][col * HP + row] = pc[q];
                     }
                 __syncthreads();
                 writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
@@ -618,29 +657,38 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
             }
             if (step1) writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
             if (nb > 0) {
-                // GEMM2: warp -> columns warp*8.. (one n-tile), t = 0..31 (two m-tiles), K = 64 rows
+                // GEMM2: warp -> columns warp*8.. (one n-tile), t = 0..31 (two m-tiles), K = 64 rows;
+                // the tile's sum starts at zero and is folded into acc2 with IEEE FP32 adds
+                float tile2[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) tile2[mt][h] = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < RT; kk += 16) {
-                    uint32_t bh[2], bl[2];
+                    uint32_t bf[P][2];
                     const int nrow = warp * 8 + (lane & 7);
                     const int kc = kk + ((lane >> 3) & 1) * 8;
-                    ldsm2(bh, s.Xh + nrow * HP + kc);
-                    if (SPLIT) ldsm2(bl, s.Xl + nrow * HP + kc);
+#pragma unroll
+                    for (int q = 0; q < P; ++q) ldsm2(bf[q], s.X3[q] + nrow * HP + kc);
+                    uint32_t b0[P], b1[P];
+#pragma unroll
+                    for (int q = 0; q < P; ++q) b0[q] = bf[q][0], b1[q] = bf[q][1];
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {
                         if (mt * 16 >= nb) continue;
-                        uint32_t ah[4], al[4];
+                        uint32_t af[P][4];
                         const int mrow = mt * 16 + (j8 & 1) * 8 + (lane & 7);
                         const int kcol = kk + (j8 >> 1) * 8;
-                        ldsm4(ah, s.Vh + mrow * HP + kcol);
-                        if (SPLIT) {
-                            ldsm4(al, s.Vl + mrow * HP + kcol);
-                            Tc<PREC>::mma(acc2[mt], al, bh[0], bh[1]);
-                            Tc<PREC>::mma(acc2[mt], ah, bl[0], bl[1]);
-                        }
-                        Tc<PREC>::mma(acc2[mt], ah, bh[0], bh[1]);
+#pragma unroll
+                        for (int q = 0; q < P; ++q) ldsm4(af[q], s.V3[q] + mrow * HP + kcol);
+                        mma_pieces<PREC>(tile2[mt], af, b0, b1);
                     }
                 }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) acc2[mt][h] += tile2[mt][h];
             }
             __syncthreads();     // the buffers are refilled by the next iteration
         }
@@ -719,7 +767,7 @@ __device__ void refine_body(const PanelArgs& a, const PanelSmem& s, int64_t r0, 
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
+__global__ void __launch_bounds__(kPT, PREC == 0 ? 2 : 1) ism_panel_kernel(PanelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // persistent: L, gamma, W, Bf, W'; tile buffers; the factor's temporaries G, beta, B
     // alias the X tile buffers (they are dead between sweeps)
@@ -747,14 +795,19 @@ __global__ void __launch_bounds__(kPT) ism_panel_kernel(PanelArgs a) {
     s.cb = s.Bt + kPB * kPB;
     {
         unsigned short* h = reinterpret_cast<unsigned short*>(reinterpret_cast<void**>(s.flag + 4) + 2 * CT + 2 * kPB);
-        s.Uh = h; h += kPB * HP;
-        s.Ul = h; h += kPB * HP;
-        s.Wh = h; h += CT * WPT;
-        s.Wl = h; h += CT * WPT;
-        s.Xh = h; h += CT * HP;
-        s.Xl = h; h += CT * HP;
-        s.Vh = h; h += kPB * HP;
-        s.Vl = h;
+        constexpr int NP = PREC == 0 ? 0 : Tc<PREC == 0 ? 1 : PREC>::pieces;
+        s.U3[0] = h; h += NP > 0 ? kPB * HP : 0;
+        s.W3[0] = h; h += NP > 0 ? CT * WPT : 0;
+        s.X3[0] = h; h += NP > 0 ? CT * HP : 0;
+        s.V3[0] = h; h += NP > 0 ? kPB * HP : 0;
+        s.U3[1] = h; h += NP > 1 ? kPB * HP : 0;
+        s.W3[1] = h; h += NP > 1 ? CT * WPT : 0;
+        s.X3[1] = h; h += NP > 1 ? CT * HP : 0;
+        s.V3[1] = h; h += NP > 1 ? kPB * HP : 0;
+        s.U3[2] = h; h += NP > 2 ? kPB * HP : 0;
+        s.W3[2] = h; h += NP > 2 ? CT * WPT : 0;
+        s.X3[2] = h; h += NP > 2 ? CT * HP : 0;
+        s.V3[2] = h;
     }
     static_assert(3 * kPB * kPB + kPB <= 2 * CT * XLD, "factor temporaries fit the tiles");
 
@@ -835,13 +888,16 @@ size_t panel_smem(int prec) {
     const size_t base = sizeof(double) * (kPB + 32) +
                         sizeof(float) * (3 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16 +
                         sizeof(void*) * (2 * CT + 2 * kPB);
-    const size_t tc = sizeof(unsigned short) * 2 * (2 * kPB * HP + CT * WPT + CT * HP);
-    return base + (prec ? tc : 0);
+    const int pieces = prec == 1 ? 2 : prec == 2 ? 1 : prec == 3 ? 3 : 0;
+    const size_t tc = sizeof(unsigned short) * pieces * (2 * kPB * HP + CT * WPT + CT * HP);
+    return base + tc;
 }
 
 const void* panel_kernel_ptr(int prec) {
-    return prec == 1 ? (const void*)ism_panel_kernel<1>
-                     : prec == 2 ? (const void*)ism_panel_kernel<2> : (const void*)ism_panel_kernel<0>;
+    return prec == 1   ? (const void*)ism_panel_kernel<1>
+           : prec == 2 ? (const void*)ism_panel_kernel<2>
+           : prec == 3 ? (const void*)ism_panel_kernel<3>
+                       : (const void*)ism_panel_kernel<0>;
 }
 
 }  // namespace

@@ -31,6 +31,7 @@ ENKF_FP32 = 1
 ENKF_PANEL_BF16 = 2
 ENKF_PANEL_FP16 = 3
 ENKF_PANEL_FP32 = 4
+ENKF_PANEL_BF16X3 = 5
 
 ENKF_FLAG_REFINE = 0x1
 ENKF_FLAG_NO_CHECKS = 0x2

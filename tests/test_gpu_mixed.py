@@ -2,8 +2,10 @@
 
 ENKF_PANEL_BF16 runs the trailing update and the dots on tensor cores with split
 BF16 operands (x = hi + lo, three products; each operand kept to ~2^-17);
-ENKF_PANEL_FP16 uses one FP16 product (unit roundoff 2^-11).  Both store in FP32,
-accumulate in FP32 and form the level denominators in FP64.  Tolerances WITHOUT
+ENKF_PANEL_FP16 uses one FP16 product (unit roundoff 2^-11); ENKF_PANEL_BF16X3 splits
+each operand in three BF16 pieces (six products, operands kept to ~2^-25, the FP32
+bars of the plain path).  All store in FP32, accumulate in FP32 and form the level
+denominators in FP64.  Tolerances WITHOUT
 refinement, stated per result (relative Frobenius error against the oracle on the
 same FP32 inputs; M = V^T Z carries the conditioning of R + V V^T, hence the
 gamma factor):
@@ -11,6 +13,7 @@ gamma factor):
     mode          Z       X_A      M
     PANEL_BF16    1e-4    5e-5     2e-5 * max(1, gamma_max/10)
     PANEL_FP16    5e-3    1e-3     2e-3 * max(1, gamma_max/10)
+    PANEL_BF16X3  1e-5    1e-5     1e-6 * max(1, gamma_max/10)
 
 The measured errors are printed so the tables in the design notes can quote them.
 """
@@ -31,9 +34,13 @@ from paper_1302_3876_gb300 import enkf  # noqa: E402
 BARS = {
     enkf.ENKF_PANEL_BF16: {"Z": 1e-4, "XA": 5e-5, "M": 2e-5},
     enkf.ENKF_PANEL_FP16: {"Z": 5e-3, "XA": 1e-3, "M": 2e-3},
+    enkf.ENKF_PANEL_BF16X3: {"Z": 1e-5, "XA": 1e-5, "M": 1e-6},
 }
-NAME = {enkf.ENKF_PANEL_BF16: "PANEL_BF16", enkf.ENKF_PANEL_FP16: "PANEL_FP16"}
-GAMMA_REL = {enkf.ENKF_PANEL_BF16: 1e-4, enkf.ENKF_PANEL_FP16: 1e-3}   # ~ 2^-17 and 2^-11 operands
+NAME = {enkf.ENKF_PANEL_BF16: "PANEL_BF16", enkf.ENKF_PANEL_FP16: "PANEL_FP16",
+        enkf.ENKF_PANEL_BF16X3: "PANEL_BF16X3"}
+# ~ 2^-17, 2^-11 and 2^-25 operands
+GAMMA_REL = {enkf.ENKF_PANEL_BF16: 1e-4, enkf.ENKF_PANEL_FP16: 1e-3, enkf.ENKF_PANEL_BF16X3: 1e-5}
+TC_MODES = [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16, enkf.ENKF_PANEL_BF16X3]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,7 +99,7 @@ def check(mode, dev, r, V, D, dXB, label):
     assert dev["info"].gamma_max == pytest.approx(gamma.max(), rel=GAMMA_REL[mode])
 
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16])
+@pytest.mark.parametrize("mode", TC_MODES)
 @pytest.mark.parametrize("nobs,nens,panel_b", [(1, 4, 0), (31, 5, 0), (129, 16, 8), (4099, 64, 32), (20000, 48, 16),
                                                (20011, 128, 32), (9000, 256, 32), (5000, 37, 5)])
 def test_tensor_core_panel_random(mode, nobs, nens, panel_b):
@@ -102,7 +109,7 @@ def test_tensor_core_panel_random(mode, nobs, nens, panel_b):
     check(mode, dev, r, V, D, dXB, f"nobs={nobs} nens={nens} b={panel_b}")
 
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16])
+@pytest.mark.parametrize("mode", TC_MODES)
 def test_large_single_full_size(mode):
     w = synth.large_single(dtype=np.float32)
     dXB = w["dXB"].astype(np.float64)
@@ -136,10 +143,11 @@ def test_panel_single_full_size():
 # rho < 1 (the medium cases below); at gamma ~ 10^4 it is not effective and is
 # not tested there.
 # ---------------------------------------------------------------------------
-GAIN_MODES = (enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP32)
+GAIN_MODES = (enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP32, enkf.ENKF_PANEL_BF16X3)
 
 
-@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16, enkf.ENKF_PANEL_FP32])
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16, enkf.ENKF_PANEL_FP32,
+                                  enkf.ENKF_PANEL_BF16X3])
 @pytest.mark.parametrize("nobs,nens,panel_b", [(129, 16, 8), (20011, 128, 32), (9000, 256, 32), (5000, 37, 5)])
 def test_refinement_random(mode, nobs, nens, panel_b):
     nstate = 3 * nobs + 1
