@@ -55,7 +55,8 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        off_delta, off_P, off_Md, total;
+        off_delta, off_P, off_Md, off_vp, off_up, total;
+    int64_t ldp;              // row pitch of the 16-bit operand pieces (tensor-core panel modes)
     bool refine;
     // latched status of the previous call
     int* h_status;            // pinned host word
@@ -166,6 +167,14 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
     p->off_M = o; o = align256(o + p->w * N * N);
     p->off_M64 = o; o = align256(o + sizeof(double) * N * N);
     p->off_Msplit = o; o = align256(o + xa_split_bytes(nens));
+    {
+        // tensor-core panel modes: pieces of V ([pieces][N][ldp]) and of two panels' U_P
+        // ([2][pieces][b_max][ldp]), 16-bit
+        const int pieces = panel ? panel_pieces(p->P.prec) : 0;
+        p->ldp = (nobs + 63 + 7) / 8 * 8;
+        p->off_vp = o; o = align256(o + sizeof(uint16_t) * (size_t)pieces * N * p->ldp);
+        p->off_up = o; o = align256(o + sizeof(uint16_t) * 2 * (size_t)pieces * panel_max_b() * p->ldp);
+    }
     p->refine = panel && (flags & ENKF_FLAG_REFINE);
     if (p->refine) {
         p->off_delta = o; o = align256(o + sizeof(float) * (size_t)p->ldzw * N);
@@ -353,6 +362,9 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.timeout_ns = a.timeout_ns;
         pa.refine = 0;
         pa.Qg = nullptr;
+        pa.vp = (unsigned short*)(ws + p->off_vp);
+        pa.up = (unsigned short*)(ws + p->off_up);
+        pa.ldp = p->ldp;
         CU(panel_launch(p->P, pa, s), "panel launch");
         panel_args = pa;
     } else {

@@ -69,6 +69,10 @@ struct PanelArgs {
     int32_t refine;                // 1: stored-factor recurrence on the columns in Z (R^-1 times a residual)
     const double* Qg;              // [nens][nens] Gram V^T U of the final U columns (refinement)
     uint64_t timeout_ns;
+    // tensor-core modes: 16-bit operand pieces prepared once in the workspace
+    unsigned short* vp;            // [pieces][nens][ldp]   pieces of V (written by the Step-1 sweep)
+    unsigned short* up;            // [2][pieces][kPB][ldp] pieces of each panel's U_P (two buffers)
+    int64_t ldp;                   // row pitch of vp / up (multiple of 8, >= nobs + 63)
 };
 
 struct PanelLaunch {
@@ -82,6 +86,7 @@ struct PanelLaunch {
 };
 
 int panel_max_b();
+int panel_pieces(int prec);   // 16-bit operand pieces of the tensor-core variants (0: FP32 cores)
 cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, PanelLaunch* out);
 cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
 

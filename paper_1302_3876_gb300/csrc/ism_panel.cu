@@ -69,6 +69,9 @@ struct PanelSmem {
 };
 constexpr int HP = RT + 8;     // 16-bit tile pitch along rows
 constexpr int WPT = kPB + 8;   // 16-bit tile pitch along t
+// 16-bit elements of one operand piece (U3 and V3 two stages, W3, X3): piece q of an array
+// is piece 0 plus q * kPiece
+constexpr int kPiece = 4 * kPB * HP + CT * WPT + CT * HP;
 
 __device__ __forceinline__ float* col_ptr(const PanelArgs& a, int c) {
     return c < a.nens ? static_cast<float*>(a.U) + (int64_t)c * a.ldu
@@ -524,7 +527,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                 if (t < bp)
                     for (int u = 0; u < bp; ++u) v = fmaf(s.W[t * kPB + u], As[u * CT + c], v);
                 unsigned short pc[3];
-                split_pieces<PREC>(v, pc);
+                split_pieces<PREC>(-v, pc);   // -W': GEMM1 multiplies the pieces of +U_P
 #pragma unroll
                 for (int q = 0; q < P; ++q) s.W3[q][c * WPT + t] = pc[q];
             }
@@ -555,13 +558,31 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
         auto pdst = [&](int c) { return s.pdst[c]; };
         auto pu = [&](int t) { return s.pu[t]; };
         auto pv = [&](int t) { return s.pv[t]; };
+        const bool mat_here = (opts & kMaterialize) && c0 + CT >= ncols;
+        const int pidx = bp > 0 ? k0 / a.panel_b : 0;
+        const int64_t uplane = (int64_t)kPB * a.ldp, ubuf = P * uplane, vplane = (int64_t)N * a.ldp;
         auto stage = [&](int tile, int buf) {
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
             const int64_t row0 = r0 + rr;
             stage_cols<VEC>(s.Xs + buf * CT * XLD, XLD, CT, ncl, row0, nr, psrc);
-            if (bp > 0) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, pu);
-            if (nb > 0) stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, pv);
+            if (bp > 0) {
+                if (mat_here) stage_cols<VEC>(s.UPs + buf * kPB * RT, RT, bp, bp, row0, nr, pu);
+                // pieces of U_P and V_{P'}: [t][row] tiles, 16-byte copies of 8 rows, zero past nr / bp / nb
+                for (int e = tid; e < 2 * P * kPB * (RT / 8); e += kPT) {
+                    const int j8r = (e & 7) * 8, t = (e >> 3) % kPB, q = (e >> 3) / kPB % P, isv = e / (P * kPB * 8);
+                    const int lim = isv ? nb : bp;
+                    const int rem = nr - j8r;
+                    const int bytes = (t < lim && rem > 0) ? (rem >= 8 ? 16 : 2 * rem) : 0;
+                    const unsigned short* src =
+                        isv ? a.vp + q * vplane + (int64_t)(kv + (t < lim ? t : 0)) * a.ldp + row0 + j8r
+                            : a.up + (pidx & 1) * ubuf + q * uplane + (int64_t)(t < lim ? t : 0) * a.ldp + row0 + j8r;
+                    unsigned short* dst = (isv ? s.V3[0] : s.U3[0]) + q * kPiece + buf * kPB * HP + t * HP + j8r;
+                    cp_async16(dst, bytes ? src : a.vp, bytes);
+                }
+            } else if (nb > 0) {
+                stage_cols<VEC>(s.VNs + buf * kPB * RT, RT, nb, nb, row0, nr, pv);
+            }
             cp_async_commit();
         };
         __syncthreads();
@@ -580,24 +601,39 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
             const float* vns = s.VNs + buf * kPB * RT;
             const int64_t rr = (int64_t)tile * RT;
             const int nr = (int)min((int64_t)RT, nrows - rr);
+            const int64_t row0 = r0 + rr;
             if (step1) {
+                // pieces of the staged V columns (the source of U), kept for the later sweeps
+                for (int e = tid; e < CT * (RT / 4); e += kPT) {
+                    const int c = e >> 4, r4 = (e & 15) * 4;
+                    const int cc = trail_col(c0 + c, N, k1);
+                    if (c < ncl && cc < N && r4 < nr)
+                        put4<PREC>(a.vp + cc * a.ldp, a.vp + vplane + cc * a.ldp, a.vp + 2 * vplane + cc * a.ldp,
+                                   (int)(row0 + r4), *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
+                }
+                __syncthreads();
                 scale_tile(xs, r, r0 + rr, nr);
                 __syncthreads();
-            }
-            // 16-bit operand tiles: -U_P [t][row], V' [t][row] (zero rows t >= bp / nb)
-            for (int e = tid; e < kPB * (RT / 4); e += kPT) {
-                const int t = e >> 4, r4 = (e & 15) * 4;
-                if (bp > 0) {
-                    float4 u = t < bp ? *reinterpret_cast<const float4*>(&ups[t * RT + r4]) : make_float4(0, 0, 0, 0);
-                    u.x = -u.x, u.y = -u.y, u.z = -u.z, u.w = -u.w;
-                    put4<PREC>(s.U3[0], s.U3[1], s.U3[2], t * HP + r4, u);
-                }
-                if (nb > 0) {
-                    const float4 v = t < nb ? *reinterpret_cast<const float4*>(&vns[t * RT + r4]) : make_float4(0, 0, 0, 0);
-                    put4<PREC>(s.V3[0], s.V3[1], s.V3[2], t * HP + r4, v);
-                }
+                // pieces of panel 0's U_P = the first columns of U after Step 1
+                if (c0 == 0)
+                    for (int e = tid; e < kPB * (RT / 4); e += kPT) {
+                        const int c = e >> 4, r4 = (e & 15) * 4;
+                        if (c < ncl && c < N && c < a.panel_b && r4 < nr)
+                            put4<PREC>(a.up + c * a.ldp, a.up + uplane + c * a.ldp, a.up + 2 * uplane + c * a.ldp,
+                                       (int)(row0 + r4), *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
+                    }
             }
             if (bp == 0) {
+                // first sweep: V' tile pieces from the staged FP32 columns (zero rows t >= nb)
+                for (int e = tid; e < kPB * (RT / 4); e += kPT) {
+                    const int t = e >> 4, r4 = (e & 15) * 4;
+                    if (nb > 0) {
+                        const float4 v =
+                            t < nb ? *reinterpret_cast<const float4*>(&vns[t * RT + r4]) : make_float4(0, 0, 0, 0);
+                        put4<PREC>(s.V3[0] + buf * kPB * HP, s.V3[1] + buf * kPB * HP, s.V3[2] + buf * kPB * HP,
+                                   t * HP + r4, v);
+                    }
+                }
                 for (int e = tid; e < CT * (RT / 4); e += kPT) {
                     const int c = e >> 4, r4 = (e & 15) * 4;
                     put4<PREC>(s.X3[0], s.X3[1], s.X3[2], c * HP + r4,
@@ -621,7 +657,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                     const int kr = kk + (j8 >> 1) * 8 + (lane & 7);
                     const int mr = mt * 16 + (j8 & 1) * 8;
 #pragma unroll
-                    for (int q = 0; q < P; ++q) ldsm4t(af[q], s.U3[q] + kr * HP + mr);
+                    for (int q = 0; q < P; ++q) ldsm4t(af[q], s.U3[q] + buf * kPB * HP + kr * HP + mr);
 #pragma unroll
                     for (int np = 0; np < 2; ++np) {
                         const int nr2 = nb0 + np * 16 + (j8 >> 1) * 8 + (lane & 7);
@@ -653,7 +689,18 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                     }
                 __syncthreads();
                 writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
-                if ((opts & kMaterialize) && c0 + CT >= ncols) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
+                if (c0 == 0) {
+                    // pieces of the next panel's U_P: trailing columns 0.. = u_{k1..} after this panel
+                    const int nbn = min(a.panel_b, N - k1);
+                    unsigned short* ub = a.up + ((pidx + 1) & 1) * ubuf;
+                    for (int e = tid; e < kPB * (RT / 4); e += kPT) {
+                        const int c = e >> 4, r4 = (e & 15) * 4;
+                        if (c < nbn && c < ncl && r4 < nr)
+                            put4<PREC>(ub + c * a.ldp, ub + uplane + c * a.ldp, ub + 2 * uplane + c * a.ldp,
+                                       (int)(row0 + r4), *reinterpret_cast<const float4*>(&xs[c * XLD + r4]));
+                    }
+                }
+                if (mat_here) materialize_tile(a, s, ups, k0, bp, r0 + rr, nr);
             }
             if (step1) writeback_tile<VEC>(xs, ncl, r0 + rr, nr, pdst);
             if (nb > 0) {
@@ -681,7 +728,7 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
                         const int mrow = mt * 16 + (j8 & 1) * 8 + (lane & 7);
                         const int kcol = kk + (j8 >> 1) * 8;
 #pragma unroll
-                        for (int q = 0; q < P; ++q) ldsm4(af[q], s.V3[q] + mrow * HP + kcol);
+                        for (int q = 0; q < P; ++q) ldsm4(af[q], s.V3[q] + buf * kPB * HP + mrow * HP + kcol);
                         mma_pieces<PREC>(tile2[mt], af, b0, b1);
                     }
                 }
@@ -796,15 +843,16 @@ __global__ void __launch_bounds__(kPT, PREC == 0 ? 2 : 1) ism_panel_kernel(Panel
     {
         unsigned short* h = reinterpret_cast<unsigned short*>(reinterpret_cast<void**>(s.flag + 4) + 2 * CT + 2 * kPB);
         constexpr int NP = PREC == 0 ? 0 : Tc<PREC == 0 ? 1 : PREC>::pieces;
-        s.U3[0] = h; h += NP > 0 ? kPB * HP : 0;
+        // U3 and V3 hold two stages ([stage][t][row]); W3 and X3 one
+        s.U3[0] = h; h += NP > 0 ? 2 * kPB * HP : 0;
         s.W3[0] = h; h += NP > 0 ? CT * WPT : 0;
         s.X3[0] = h; h += NP > 0 ? CT * HP : 0;
-        s.V3[0] = h; h += NP > 0 ? kPB * HP : 0;
-        s.U3[1] = h; h += NP > 1 ? kPB * HP : 0;
+        s.V3[0] = h; h += NP > 0 ? 2 * kPB * HP : 0;
+        s.U3[1] = h; h += NP > 1 ? 2 * kPB * HP : 0;
         s.W3[1] = h; h += NP > 1 ? CT * WPT : 0;
         s.X3[1] = h; h += NP > 1 ? CT * HP : 0;
-        s.V3[1] = h; h += NP > 1 ? kPB * HP : 0;
-        s.U3[2] = h; h += NP > 2 ? kPB * HP : 0;
+        s.V3[1] = h; h += NP > 1 ? 2 * kPB * HP : 0;
+        s.U3[2] = h; h += NP > 2 ? 2 * kPB * HP : 0;
         s.W3[2] = h; h += NP > 2 ? CT * WPT : 0;
         s.X3[2] = h; h += NP > 2 ? CT * HP : 0;
         s.V3[2] = h;
@@ -889,7 +937,7 @@ size_t panel_smem(int prec) {
                         sizeof(float) * (3 * kPB * kPB + kPB * CT + 2 * CT * XLD + 4 * kPB * RT + kScratch) + 16 +
                         sizeof(void*) * (2 * CT + 2 * kPB);
     const int pieces = prec == 1 ? 2 : prec == 2 ? 1 : prec == 3 ? 3 : 0;
-    const size_t tc = sizeof(unsigned short) * pieces * (2 * kPB * HP + CT * WPT + CT * HP);
+    const size_t tc = sizeof(unsigned short) * pieces * (4 * kPB * HP + CT * WPT + CT * HP);
     return base + tc;
 }
 
@@ -903,6 +951,8 @@ const void* panel_kernel_ptr(int prec) {
 }  // namespace
 
 int panel_max_b() { return kPB; }
+
+int panel_pieces(int prec) { return prec == 1 ? 2 : prec == 2 ? 1 : prec == 3 ? 3 : 0; }
 
 cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, PanelLaunch* L) {
     int dev = 0, nsm = 0, occ = 0;
@@ -920,7 +970,7 @@ cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, Pane
     const int64_t by_rows = (nobs + RT - 1) / RT;
     if (grid > by_rows) grid = by_rows;
     int64_t rpb = (nobs + grid - 1) / grid;
-    rpb = (rpb + 3) / 4 * 4;
+    rpb = (rpb + 7) / 8 * 8;   // 16-byte aligned rows of the 16-bit piece arrays
     grid = (nobs + rpb - 1) / rpb;
     L->grid = (int)grid;
     L->threads = kPT;
