@@ -44,7 +44,12 @@ __global__ void observe_kernel(int64_t nobs, int n, int stride, const T* __restr
     const int e = blockIdx.y;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nobs; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = j * stride;
-        V[(int64_t)e * ldv + j] = (T)((double)dXB[(int64_t)e * ldx + i] * scale);
+        // FP32 storage scales in FP32 (one extra rounding of 1/sqrt(N-1)): FP64 arithmetic per
+        // element would run on GB300's narrow FP64 pipe
+        if (sizeof(T) == 4)
+            V[(int64_t)e * ldv + j] = dXB[(int64_t)e * ldx + i] * (T)scale;
+        else
+            V[(int64_t)e * ldv + j] = (T)((double)dXB[(int64_t)e * ldx + i] * scale);
         if (Y) D[(int64_t)e * ldd + j] = Y[(int64_t)e * ldy + j] - XB[(int64_t)e * ldb + i];
     }
 }
