@@ -454,7 +454,8 @@ def _events_ms(fn, k):
 
 def run_panel_single(args):
     """Nstate = 2^22, Nobs = 2^20 (every 4th), Nens = 256: the tensor-core panel forms (split BF16 and
-    FP16, each with one refinement step), the FP32-core panel form, and the plain FP64 path."""
+    FP16, each also with one refinement step; three-piece BF16), the FP32-core panel form, and the plain
+    FP64 path."""
     import numpy as np
     import torch
     import synth
@@ -474,7 +475,8 @@ def run_panel_single(args):
     outs = {}
     for name, mode, flags in (("bf16+refine", enkf.ENKF_PANEL_BF16, enkf.ENKF_FLAG_REFINE),
                               ("fp16+refine", enkf.ENKF_PANEL_FP16, enkf.ENKF_FLAG_REFINE),
-                              ("bf16", enkf.ENKF_PANEL_BF16, 0), ("panel32", enkf.ENKF_PANEL_FP32, 0)):
+                              ("bf16", enkf.ENKF_PANEL_BF16, 0), ("bf16x3", enkf.ENKF_PANEL_BF16X3, 0),
+                              ("panel32", enkf.ENKF_PANEL_FP32, 0)):
         plan = enkf.Plan(nstate, nobs, nens, mode, flags=flags, device=dev)
 
         def step():
