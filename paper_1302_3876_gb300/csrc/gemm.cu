@@ -223,6 +223,15 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
     return (int32_t)s;
 }
 
+static cudaError_t gram_tc_reduce(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B,
+                                  int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
+    cudaError_t e = gram_tc(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, s);
+    if (e != cudaSuccess) return e;
+    const int64_t nn = (int64_t)n * n;
+    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, nsplit, Qpart, Q, full);
+    return cudaGetLastError();
+}
+
 static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
                                int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
     const int nt = (n + GT - 1) / GT;
@@ -234,8 +243,7 @@ static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* 
         gram_upper_kernel<double><<<grid, 256, 0, s>>>(nrows, n, (const double*)A, lda, (const double*)B, ldb, rps, Qpart,
                                                        full);
     else
-        gram_upper_kernel<float><<<grid, 256, 0, s>>>(nrows, n, (const float*)A, lda, (const float*)B, ldb, rps, Qpart,
-                                                      full);
+        return gram_tc_reduce(nrows, n, (const float*)A, lda, (const float*)B, ldb, Qpart, nsplit, Q, full, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
