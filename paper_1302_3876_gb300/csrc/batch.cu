@@ -260,17 +260,35 @@ __device__ void panel_z_coefficients(const BatchDesc& d, const SmemB& s, float* 
     __syncthreads();
 }
 
-// Final values of the panel's own columns, u_m^(m-1) = gamma_m U_P B[:,m], in place.
+// Final values of the panel's own columns, u_m^(m-1) = gamma_m U_P B[:,m] = U_P beta_m, in
+// place.  beta[u][m] = 0 for u > m, so each output sums over every u < bp in the order of
+// the triangular sum; the rows of beta are read four at a time.
+template <int B>
 __device__ void panel_final_columns(const BatchDesc& d, float* X, const SmemB& s, int k0, int bp) {
     for (int j = threadIdx.x; j < d.nobs; j += kBT) {
         float* row = X + (int64_t)j * d.ldX + k0;
-        float u[kBmax];
-        for (int q = 0; q < bp; ++q) u[q] = row[q];
-        for (int m = 0; m < bp; ++m) {
-            float v = 0.f;
-            for (int q = 0; q <= m; ++q) v = fmaf(u[q], s.Bf[q * kBmax + m], v);
-            row[m] = v;
+        float acc[B];
+#pragma unroll
+        for (int m = 0; m < B; ++m) acc[m] = 0.f;
+        for (int u = 0; u < bp; ++u) {
+            const float x = row[u];
+            const float* bu = s.Bf + u * kBmax;
+#pragma unroll
+            for (int m = 0; m < B; m += (B >= 4 ? 4 : 1)) {
+                if (B >= 4) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(bu + m);
+                    acc[m] = fmaf(x, b4.x, acc[m]);
+                    acc[m + 1] = fmaf(x, b4.y, acc[m + 1]);
+                    acc[m + 2] = fmaf(x, b4.z, acc[m + 2]);
+                    acc[m + 3] = fmaf(x, b4.w, acc[m + 3]);
+                } else {
+                    acc[m] = fmaf(x, bu[m], acc[m]);
+                }
+            }
         }
+#pragma unroll
+        for (int m = 0; m < B; ++m)
+            if (m < bp) row[m] = acc[m];
     }
     __syncthreads();
 }
@@ -397,7 +415,7 @@ __device__ void solve_problem(const BatchDesc& d, const float* in, float* out, f
         const int k1 = k0 + bp;
         const int nb = (N - k1) < B ? (N - k1) : B;
         sweep<B>(d, X, Vr, s, k0, bp, k1, nb, true);
-        panel_final_columns(d, X, s, k0, bp);
+        panel_final_columns<B>(d, X, s, k0, bp);
     }
     finish_problem(d, out, X, Vr, s.tile, s.apart, Ch, ws + d.Qw);
 }
