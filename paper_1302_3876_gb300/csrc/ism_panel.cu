@@ -163,12 +163,14 @@ __device__ __forceinline__ void stage_cols(float* dst, int ld, int ncols_tile, i
 constexpr int kMaterialize = 1;   // write the panel's final U columns (last column tile)
 constexpr int kStep1 = 2;         // first sweep: stage V and D, apply Step 1, write U and Z
 
-// Step 1 (eq. SM-step-1) on a staged tile: x[c][j] = x[c][j] / r_j.
+// Step 1 (eq. SM-step-1) on a staged tile: x[c][j] = x[c][j] * (1 / r_j) -- one reciprocal per
+// row and a product per element (at most one rounding more than a division).
 __device__ __forceinline__ void scale_tile(float* xs, const float* r, int64_t row0, int nr) {
     const int j = threadIdx.x & 63;
     if (j < nr) {
-        const float rj = r[row0 + j];
-        for (int c = threadIdx.x >> 6; c < CT; c += kPT / 64) xs[c * XLD + j] = xs[c * XLD + j] / rj;
+        const float inv = 1.0f / r[row0 + j];
+#pragma unroll 4
+        for (int c = threadIdx.x >> 6; c < CT; c += kPT / 64) xs[c * XLD + j] = xs[c * XLD + j] * inv;
     }
 }
 
