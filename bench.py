@@ -451,10 +451,11 @@ def run_ours(args):
         "roofline": roofline,
         "phases_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in phases.items()},
         "phase_share": {k: v[0] / total_ms for k, v in phases.items()} if total_ms > 0 else {},
-        "e2e": {"value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "note": "pinned host buffers; copies in, compute and copies out of consecutive steps overlap "
-                        "on three streams (two device buffer sets)"},
+        "e2e": None if args.no_e2e else {
+            "value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+            "note": "pinned host buffers; copies in, compute and copies out of consecutive steps overlap "
+                    "on three streams (two device buffer sets)"},
         "gpu_launches": 7 * args.steps,   # prep, solve, Gram (2), M, split of M, X_A
         "clocks": clk.summary(),
         "comparator_fp64": fp64,

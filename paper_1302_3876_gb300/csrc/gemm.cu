@@ -225,10 +225,11 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
 
 static cudaError_t gram_tc_reduce(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B,
                                   int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
-    cudaError_t e = gram_tc(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, s);
+    int32_t used = 0;
+    cudaError_t e = gram_tc(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, s, &used);
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
-    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, nsplit, Qpart, Q, full);
+    gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, used, Qpart, Q, full);
     return cudaGetLastError();
 }
 

@@ -199,16 +199,26 @@ __global__ void __launch_bounds__(kThreads) gram_tc_kernel(int64_t nrows, int n,
 }  // namespace
 
 cudaError_t gram_tc(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
-                    double* Qpart, int32_t nsplit, int full, cudaStream_t s) {
+                    double* Qpart, int32_t nsplit, int full, cudaStream_t s, int32_t* used) {
     const int nt = (n + QT - 1) / QT;
     const int tiles = full ? nt * nt : nt * (nt + 1) / 2;
-    int64_t rps = (nrows + nsplit - 1) / nsplit;
-    rps = (rps + QR - 1) / QR * QR;
     const bool vec = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && (lda % 4 == 0) && (ldb % 4 == 0);
     const void* fn = vec ? (const void*)gram_tc_kernel<true> : (const void*)gram_tc_kernel<false>;
     const int smem = (int)sizeof(GramSmem);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    // One wave: a grid larger than the resident CTAs leaves a partial last wave (e.g. 609 CTAs
+    // on 304 slots run as 304 + 304 + 1), so the rows are cut into at most slots / tiles slices.
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem)) != cudaSuccess) return e;
+    const int64_t wave = (int64_t)sms * (per_sm > 0 ? per_sm : 1) / tiles;
+    if (wave >= 1 && nsplit > wave) nsplit = (int32_t)wave;
+    if (nsplit < 1) nsplit = 1;
+    int64_t rps = (nrows + nsplit - 1) / nsplit;
+    rps = (rps + QR - 1) / QR * QR;
+    *used = nsplit;
     dim3 grid(tiles, nsplit);
     if (vec)
         gram_tc_kernel<true><<<grid, kThreads, smem, s>>>(nrows, n, A, lda, B, ldb, rps, Qpart, full);

@@ -96,9 +96,11 @@ cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64
                        int64_t ldb, double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
 int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
 // FP32 operands: the partial Grams on tensor cores (three BF16 pieces per operand, six products,
-// 32-row stages folded into FP32 and every 512 rows into FP64); Qpart as for gram_upper.
+// 32-row stages folded into FP32 and every 512 rows into FP64); Qpart as for gram_upper.  At most
+// nsplit row slices are used -- fewer where nsplit slices would not fit one wave of resident CTAs;
+// *used receives the count, the number of partial Grams written.
 cudaError_t gram_tc(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
-                    double* Qpart, int32_t nsplit, int full, cudaStream_t s);
+                    double* Qpart, int32_t nsplit, int full, cudaStream_t s, int32_t* used);
 // Full Gram P[k][m] = sum_j A[j,k] B[j,m] (every k, m), same splitting and fixed-order reduction.
 cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
                       double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
