@@ -14,6 +14,9 @@
 //               chunk marks its accumulator full.  Two accumulators in TMEM.
 //   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4).. (its 32 rows) for one
 //               half of the columns; X_A = X_B + acc with coalesced column accesses.
+//   warp 18     X_B loader (Nens <= 128 and a TMA-aligned X_B): TMA copies of the tile's
+//               X_B chunks into a ring the epilogue reads, so the epilogue waits on no
+//               global load; each half of the epilogue then takes whole 32-member chunks.
 // M is pre-split into hi/lo images of the same layout; they stay in shared memory for
 // the whole launch when they fit (Nens <= 128), else each chunk's part travels in the
 // operand slot.  Every mbarrier wait is bounded (iteration count and %globaltimer); on
@@ -32,9 +35,10 @@ namespace {
 constexpr int XM = 128;     // rows per tile (MMA M)
 constexpr int XKC = 32;     // K per chunk: two MMA K-steps of 16
 constexpr int XRS = 4;      // raw (FP32) slots
+constexpr int XBS = 4;      // X_B slots (one tile of Nens <= 128)
 constexpr int XNMAX = 256;  // largest MMA N
 constexpr int kEpi = 256, kConv = 256;
-constexpr int kThreads = kEpi + kConv + 64;    // + loader warp + MMA warp
+constexpr int kThreads = kEpi + kConv + 96;    // + loader warp + MMA warp + X_B loader warp
 constexpr int kRawBytes = XM * XKC * 4;        // one raw chunk
 constexpr int kABytes = 2 * XM * XKC * 2;      // A hi + lo of one chunk
 constexpr int kMaxSmem = 232448;
@@ -64,6 +68,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
 
 struct XaShared {
     uint64_t raw_full[XRS], raw_empty[XRS], a_full[4], a_empty[4], acc_full[2], acc_empty[2], drained;
+    uint64_t xb_full[XBS], xb_empty[XBS];
     unsigned taddr;
     int err;
 };
@@ -154,7 +159,7 @@ __device__ __forceinline__ void put_row8(unsigned char* ahi, int off, const floa
 
 struct XaParams {
     int64_t nstate;
-    int nens, nb, nchunks, alloc_cols, nas, resident;
+    int nens, nb, nchunks, alloc_cols, nas, resident, xbt;
     const float* XB;
     int64_t ldb;
     const float* dXB;
@@ -167,13 +172,15 @@ struct XaParams {
 };
 
 template <bool TMA>
-__global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_constant__ CUtensorMap tmap, XaParams p) {
+__global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                              const __grid_constant__ CUtensorMap tmapb, XaParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nb = p.nb, nchunks = p.nchunks, nas = p.nas;
     const int aslot = kABytes + (p.resident ? 0 : b_chunk_bytes(nb));
     // 1024-byte aligned working area (the launch reserves 1 KB of slack for this)
     unsigned char* raw = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // XRS x kRawBytes
-    unsigned char* aring = raw + XRS * kRawBytes;                    // nas x aslot
+    unsigned char* xbs = raw + XRS * kRawBytes;                      // XBS x kRawBytes when p.xbt
+    unsigned char* aring = xbs + (p.xbt ? XBS * kRawBytes : 0);     // nas x aslot
     unsigned char* bres = aring + nas * aslot;                       // resident B images
     XaShared* sh = reinterpret_cast<XaShared*>(bres + (p.resident ? nchunks * b_chunk_bytes(nb) : 0));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -184,6 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
         for (int q = 0; q < XRS; ++q) mbar_init(&sh->raw_full[q], 1), mbar_init(&sh->raw_empty[q], kConv);
         for (int q = 0; q < nas; ++q) mbar_init(&sh->a_full[q], kConv), mbar_init(&sh->a_empty[q], 1);
         for (int q = 0; q < 2; ++q) mbar_init(&sh->acc_full[q], 1), mbar_init(&sh->acc_empty[q], kEpi);
+        for (int q = 0; q < XBS; ++q) mbar_init(&sh->xb_full[q], 1), mbar_init(&sh->xb_empty[q], kEpi / 2);
         mbar_init(&sh->drained, 1);
         sh->err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -278,7 +286,13 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
     } else if (warp < 8) {
         // ---------------- epilogue
         const int quarter = warp & 3, half = warp >> 2;
-        const int ngroups = nb / 16, g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+        const int ngroups = nb / 16;
+        int g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+        if (p.xbt) {   // whole chunks (two groups of 16 members) per half: one consumer per X_B slot
+            const int hc = (nchunks + 1) / 2;
+            g0 = half ? 2 * hc : 0;
+            g1 = half ? ngroups : min(ngroups, 2 * hc);
+        }
         int64_t t = 0;
         auto load_xb = [&](int64_t i, int gq, float* xb) {
             const int e0 = yb * nb + gq * 16;
@@ -289,6 +303,39 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
             const int b = (int)(t & 1);
             const int64_t i = tile * XM + quarter * 32 + lane;
+            if (p.xbt) {
+                if (!mbar_wait(&sh->acc_full[b], (unsigned)((t >> 1) & 1), sh, p.ctl, p.timeout_ns)) break;
+                tc_fence_after();
+                const unsigned row_addr = tbase + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * nb);
+                bool ok = true;
+                for (int gq = g0; gq < g1; gq += 2) {
+                    const int c = gq >> 1;   // X_B chunk: members 32 c .. 32 c + 31, [member][row]
+                    if (!mbar_wait(&sh->xb_full[c], (unsigned)(t & 1), sh, p.ctl, p.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const float* xs = reinterpret_cast<const float*>(xbs + c * kRawBytes) + quarter * 32 + lane;
+                    for (int h = 0; h < 2 && gq + h < g1; ++h) {
+                        unsigned acc[16];
+                        tmem_ld16(row_addr + (gq + h) * 16, acc);
+                        float xb[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) xb[q] = xs[(h * 16 + q) * XM];
+                        tmem_wait_ld();
+                        const int e0 = (gq + h) * 16;
+                        if (i < p.nstate) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
+                        }
+                    }
+                    mbar_arrive(&sh->xb_empty[c]);
+                }
+                if (!ok) break;
+                tc_fence_before();
+                mbar_arrive(&sh->acc_empty[b]);
+                continue;
+            }
             // X_B does not depend on the MMAs: the first group's loads are issued before the wait,
             // and each later group's one group ahead of its use
             float xnext[16];
@@ -313,6 +360,34 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
             }
             tc_fence_before();
             mbar_arrive(&sh->acc_empty[b]);
+        }
+    } else if (warp == 18) {
+        // ---------------- X_B loader (TMA): chunk c of each tile into slot c
+        if (TMA && p.xbt && lane == 0) {
+            int64_t t = 0;
+            int cstop = -1;   // chunk whose slot wait gave up (tile t); -1: every tile issued
+            for (int64_t tile = blockIdx.x; cstop < 0 && tile < ntiles; tile += gridDim.x, ++t) {
+                for (int c = 0; c < nchunks; ++c) {
+                    if (t >= 1 && !mbar_wait(&sh->xb_empty[c], (unsigned)((t - 1) & 1), sh, p.ctl, p.timeout_ns)) {
+                        cstop = c;
+                        break;
+                    }
+                    mbar_expect_tx(&sh->xb_full[c], kRawBytes);
+                    const int x = (int)(tile * XM), y = c * XKC;
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3}], [%4];\n" ::"r"(smem_u32(xbs + c * kRawBytes)),
+                        "l"(reinterpret_cast<uint64_t>(&tmapb)), "r"(x), "r"(y), "r"(smem_u32(&sh->xb_full[c]))
+                        : "memory");
+                }
+            }
+            // every issued copy has landed before the CTA may exit: the last fill of slot c was
+            // tile t - 1, or tile t for the slots filled before the wait gave up
+            if (cstop >= 0) --t;   // back to the tile that stopped (its loop increment ran)
+            for (int c = 0; c < nchunks; ++c) {
+                const int64_t last = (cstop >= 0 && c < cstop) ? t : t - 1;
+                if (last >= 0) mbar_drain(&sh->xb_full[c], (unsigned)(last & 1), p.timeout_ns);
+            }
         }
     } else {
         // ---------------- MMA issue (warp 17, one thread)
@@ -394,7 +469,7 @@ struct XaGeom {
     int nb, nblocks, nchunks, alloc, nas, resident, smem;
 };
 
-XaGeom xa_geom(int32_t nens) {
+XaGeom xa_geom(int32_t nens, bool xbt) {
     XaGeom g;
     const int nfirst = nens < XNMAX ? nens : XNMAX;
     g.nb = (nfirst + 15) / 16 * 16;
@@ -405,7 +480,8 @@ XaGeom xa_geom(int32_t nens) {
     g.alloc = alloc;
     g.resident = g.nchunks * b_chunk_bytes(g.nb) <= 65536;
     const int aslot = kABytes + (g.resident ? 0 : b_chunk_bytes(g.nb));
-    const int fixed = XRS * kRawBytes + (g.resident ? g.nchunks * b_chunk_bytes(g.nb) : 0) + (int)sizeof(XaShared) + 1024;
+    const int fixed = (XRS + (xbt ? XBS : 0)) * kRawBytes + (g.resident ? g.nchunks * b_chunk_bytes(g.nb) : 0) +
+                      (int)sizeof(XaShared) + 1024;
     g.nas = (kMaxSmem - fixed) / aslot;
     if (g.nas > 4) g.nas = 4;
     g.smem = fixed + g.nas * aslot;
@@ -414,17 +490,45 @@ XaGeom xa_geom(int32_t nens) {
     return g;
 }
 
+// Tiled FP32 tensor map of an nstate x nens column-major array (rows inner), box 128 rows x
+// 32 members, zero fill past the ends; false if the base or stride is not 16-byte aligned or
+// the driver entry point is unavailable.
+bool encode_rows_members(CUtensorMap* map, const float* base, int64_t nstate, int32_t nens, int64_t ld) {
+    if ((uintptr_t)base % 16 != 0 || (ld * 4) % 16 != 0) return false;
+    // resolved through the runtime so the library has no link-time dependency on libcuda
+    using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<EncodeTiled>(f);
+    }
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nstate, (cuuint64_t)nens};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {XM, XKC};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 size_t xa_split_bytes(int32_t nens) {
-    const XaGeom g = xa_geom(nens);
+    const XaGeom g = xa_geom(nens, false);
     return (size_t)g.nblocks * g.nchunks * b_chunk_bytes(g.nb);
 }
 
 cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
                            const float* M, void* msplit, float* XA, int64_t lda, Control* ctl, uint64_t timeout_ns,
                            cudaStream_t s) {
-    const XaGeom g = xa_geom(nens);
+    XaGeom g = xa_geom(nens, false);
     if (g.nas < 2) return cudaErrorInvalidConfiguration;
     {
         const int64_t total = (int64_t)g.nblocks * g.nchunks * g.nb * XKC;
@@ -435,33 +539,19 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    // TMA tensor map of dX_B (rows inner, members outer), box 128 rows x 32 members; the
-    // rows and members past the end read as zeros.  Needs 16-byte aligned base and stride.
-    CUtensorMap tmap;
+    // TMA tensor maps of dX_B and X_B (rows inner, members outer), box 128 rows x 32 members;
+    // the rows and members past the end read as zeros.  Each needs a 16-byte aligned base and
+    // stride; X_B goes through TMA only for a single column block of at most four chunks whose
+    // M images stay resident (Nens <= 128), else the epilogue loads it from global memory.
+    CUtensorMap tmap, tmapb;
     memset(&tmap, 0, sizeof(tmap));
-    bool tma = ((uintptr_t)dXB % 16 == 0) && ((ldx * 4) % 16 == 0) && nstate < (int64_t(1) << 31);
-    if (tma) {
-        const cuuint64_t dims[2] = {(cuuint64_t)nstate, (cuuint64_t)nens};
-        const cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
-        const cuuint32_t box[2] = {XM, XKC};
-        const cuuint32_t estr[2] = {1, 1};
-        // resolved through the runtime so the library has no link-time dependency on libcuda
-        using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                                         CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                         CUtensorMapFloatOOBfill);
-        static EncodeTiled encode = nullptr;
-        if (!encode) {
-            void* f = nullptr;
-            cudaDriverEntryPointQueryResult q;
-            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                    cudaSuccess &&
-                q == cudaDriverEntryPointSuccess)
-                encode = reinterpret_cast<EncodeTiled>(f);
-        }
-        tma = encode && encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(dXB), dims, strides, box,
-                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    memset(&tmapb, 0, sizeof(tmapb));
+    const bool tma = nstate < (int64_t(1) << 31) && encode_rows_members(&tmap, dXB, nstate, nens, ldx);
+    bool xbt = tma && g.nblocks == 1 && g.nchunks <= XBS && g.resident && encode_rows_members(&tmapb, XB, nstate, nens, ldb);
+    if (xbt) {
+        const XaGeom gx = xa_geom(nens, true);
+        if (gx.nas >= 2) g = gx;
+        else xbt = false;
     }
     const void* fn = tma ? (const void*)xa_tc05_kernel<true> : (const void*)xa_tc05_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
@@ -481,6 +571,7 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     p.alloc_cols = g.alloc;
     p.nas = g.nas;
     p.resident = g.resident;
+    p.xbt = xbt ? 1 : 0;
     p.XB = XB;
     p.ldb = ldb;
     p.dXB = dXB;
@@ -490,7 +581,7 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     p.lda = lda;
     p.ctl = ctl;
     p.timeout_ns = timeout_ns;
-    void* args[] = {&tmap, &p};
+    void* args[] = {&tmap, &tmapb, &p};
     return cudaLaunchKernel(fn, dim3((unsigned)gx, (unsigned)g.nblocks), dim3(kThreads), args, g.smem, s);
 }
 

@@ -134,6 +134,31 @@ def test_xa_aliases_xb(mode):
     assert rel(dev["XA"], ref["XA"]) <= TOL[mode]
 
 
+@pytest.mark.parametrize("nens,xb_pad,alias", [(40, 0, False), (100, 4, False), (128, 0, False), (128, 0, True),
+                                                (128, 1, False), (160, 0, False), (256, 4, False)])
+def test_xa_update_paths(nens, xb_pad, alias):
+    """X_A = X_B + dX_B M on the tensor-core update, every way the epilogue gets X_B: streamed
+    by TMA into shared memory (Nens <= 128 and a 16-byte aligned X_B; two epilogue halves for
+    Nens > 32), loaded from global memory (Nens > 128, or an X_B stride of an odd number of
+    floats), and X_A written over X_B.  nstate is a multiple of 4 (TMA-aligned) and leaves a
+    ragged last tile of 68 state rows."""
+    mode = enkf.ENKF_FP32
+    nobs, nstate = 700, 128 * 37 + 68
+    r, V, D, dXB, XB = random_problem(13000 + nens + 7 * xb_pad, nobs, nens, nstate)
+    ref = oracle_of(mode, r, V, D, dXB, XB)
+    plan = enkf.Plan(nstate, nobs, nens, mode)
+    tV, tD, tr = to_dev(V, np.float32), to_dev(D, np.float32), vec_dev(r, np.float32)
+    tdX = to_dev(dXB, np.float32)
+    tXB = to_dev(XB, np.float32, nstate + xb_pad)
+    tXA = tXB if alias else to_dev(np.zeros_like(XB), np.float32, nstate + 8)
+    tM = torch.zeros(nens * nens, dtype=torch.float32, device="cuda")
+    inf = plan.analysis(tr, tV, tD, dXB=tdX, XB=tXB, XA=tXA, M=tM, info=True)
+    torch.cuda.synchronize()
+    plan.close()
+    assert inf.status == 0
+    assert rel(host(tXA), ref["XA"]) <= TOL[mode]
+
+
 @pytest.mark.parametrize("panel_b", [1, 5, 8, 16, 32])
 def test_panel_widths(panel_b):
     """The panel form regroups the levels; every width (ragged last panel included)
