@@ -37,20 +37,38 @@ __global__ void center_observe_kernel(int64_t nstate, int64_t nobs, int n, int s
     }
 }
 
+// One member column per blockIdx.y; each thread takes kObsU observations kObsT apart, so
+// that kObsU independent strided loads are in flight per thread (a strided gather reads
+// every DRAM sector of the rows it spans and is bound by the loads in flight).
+constexpr int kObsT = 256, kObsU = 8;
+
 template <typename T>
-__global__ void observe_kernel(int64_t nobs, int n, int stride, const T* __restrict__ XB, int64_t ldb,
-                               const T* __restrict__ dXB, int64_t ldx, const T* __restrict__ Y, int64_t ldy,
-                               T* __restrict__ V, int64_t ldv, T* __restrict__ D, int64_t ldd, double scale) {
+__global__ void __launch_bounds__(kObsT) observe_kernel(int64_t nobs, int n, int stride, const T* __restrict__ XB,
+                                                        int64_t ldb, const T* __restrict__ dXB, int64_t ldx,
+                                                        const T* __restrict__ Y, int64_t ldy, T* __restrict__ V,
+                                                        int64_t ldv, T* __restrict__ D, int64_t ldd, double scale) {
     const int e = blockIdx.y;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nobs; j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = j * stride;
-        // FP32 storage scales in FP32 (one extra rounding of 1/sqrt(N-1)): FP64 arithmetic per
-        // element would run on GB300's narrow FP64 pipe
-        if (sizeof(T) == 4)
-            V[(int64_t)e * ldv + j] = dXB[(int64_t)e * ldx + i] * (T)scale;
-        else
-            V[(int64_t)e * ldv + j] = (T)((double)dXB[(int64_t)e * ldx + i] * scale);
-        if (Y) D[(int64_t)e * ldd + j] = Y[(int64_t)e * ldy + j] - XB[(int64_t)e * ldb + i];
+    const T* dx = dXB + (int64_t)e * ldx;
+    for (int64_t j0 = blockIdx.x * (int64_t)(kObsT * kObsU) + threadIdx.x; j0 < nobs;
+         j0 += (int64_t)gridDim.x * (kObsT * kObsU)) {
+        T d[kObsU];
+#pragma unroll
+        for (int u = 0; u < kObsU; ++u) {
+            const int64_t j = j0 + (int64_t)u * kObsT;
+            d[u] = j < nobs ? __ldcs(dx + j * stride) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kObsU; ++u) {
+            const int64_t j = j0 + (int64_t)u * kObsT;
+            if (j >= nobs) break;
+            // FP32 storage scales in FP32 (one extra rounding of 1/sqrt(N-1)): FP64 arithmetic per
+            // element would run on GB300's narrow FP64 pipe
+            if (sizeof(T) == 4)
+                V[(int64_t)e * ldv + j] = d[u] * (T)scale;
+            else
+                V[(int64_t)e * ldv + j] = (T)((double)d[u] * scale);
+            if (Y) D[(int64_t)e * ldd + j] = Y[(int64_t)e * ldy + j] - XB[(int64_t)e * ldb + j * stride];
+        }
     }
 }
 
@@ -71,15 +89,15 @@ cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int3
                                                                 (float*)dXB, ldx, (const float*)Y, ldy, (float*)V, ldv,
                                                                 (float*)D, ldd, scale);
     } else {
-        int64_t bx = (nobs + 255) / 256;
+        int64_t bx = (nobs + kObsT * kObsU - 1) / (kObsT * kObsU);
         if (bx > 4096) bx = 4096;
         dim3 grid((unsigned)bx, (unsigned)nens);
         if (fp64)
-            observe_kernel<double><<<grid, 256, 0, s>>>(nobs, nens, stride, (const double*)XB, ldb, (const double*)dXB,
+            observe_kernel<double><<<grid, kObsT, 0, s>>>(nobs, nens, stride, (const double*)XB, ldb, (const double*)dXB,
                                                         ldx, (const double*)Y, ldy, (double*)V, ldv, (double*)D, ldd,
                                                         scale);
         else
-            observe_kernel<float><<<grid, 256, 0, s>>>(nobs, nens, stride, (const float*)XB, ldb, (const float*)dXB, ldx,
+            observe_kernel<float><<<grid, kObsT, 0, s>>>(nobs, nens, stride, (const float*)XB, ldb, (const float*)dXB, ldx,
                                                        (const float*)Y, ldy, (float*)V, ldv, (float*)D, ldd, scale);
     }
     return cudaGetLastError();
