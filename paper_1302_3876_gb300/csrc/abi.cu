@@ -379,7 +379,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         if (!p->refine) {
             slot = prof_begin(p, 2, s);
             CU(gram_upper(p->fp64, p->nobs, p->nens, V, ldv, a.U, p->ldu, (double*)(ws + p->off_Qpart), p->nsplit, Q,
-                          s),
+                          ctl, a.timeout_ns, s),
                "gram launch");
             prof_end(p, slot, s);
             slot = prof_begin(p, 3, s);
@@ -400,7 +400,8 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
                                (const float*)Zp, ldzp, P, delta, p->ldzw, s),
                "refine residual");
-            CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, s), "refine Gram V^T U");
+            CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
+               "refine Gram V^T U");
             PanelArgs ra = panel_args;
             ra.Qg = Q;
             ra.refine = 1;
@@ -409,7 +410,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
             CU(cudaMemsetAsync(&ctl->barrier, 0, sizeof(unsigned), s), "barrier reset");
             CU(panel_launch(p->P, ra, s), "stored-factor correction");
-            CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, s),
+            CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, ctl, a.timeout_ns, s),
                "refine Gram V^T delta");
             CU(refine_apply(p->nobs, p->nens, (float*)Zp, ldzp, delta, p->ldzw, P, Pd, M64, (float*)Mp, s),
                "refine apply");

@@ -224,9 +224,11 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n) {
 }
 
 static cudaError_t gram_tc_reduce(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B,
-                                  int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
+                                  int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, Control* ctl,
+                                  uint64_t timeout_ns, cudaStream_t s) {
     int32_t used = 0;
-    cudaError_t e = gram_tc(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, s, &used);
+    cudaError_t e = gram_tc05(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, ctl, timeout_ns, s, &used);
+    if (e == cudaErrorNotSupported) e = gram_tc(nrows, n, A, lda, B, ldb, Qpart, nsplit, full, s, &used);
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
     gram_reduce_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, used, Qpart, Q, full);
@@ -234,7 +236,8 @@ static cudaError_t gram_tc_reduce(int64_t nrows, int32_t n, const float* A, int6
 }
 
 static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
-                               int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, cudaStream_t s) {
+                               int64_t ldb, double* Qpart, int32_t nsplit, double* Q, int full, Control* ctl,
+                               uint64_t timeout_ns, cudaStream_t s) {
     const int nt = (n + GT - 1) / GT;
     const int tiles = full ? nt * nt : nt * (nt + 1) / 2;
     int64_t rps = (nrows + nsplit - 1) / nsplit;
@@ -244,7 +247,8 @@ static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* 
         gram_upper_kernel<double><<<grid, 256, 0, s>>>(nrows, n, (const double*)A, lda, (const double*)B, ldb, rps, Qpart,
                                                        full);
     else
-        return gram_tc_reduce(nrows, n, (const float*)A, lda, (const float*)B, ldb, Qpart, nsplit, Q, full, s);
+        return gram_tc_reduce(nrows, n, (const float*)A, lda, (const float*)B, ldb, Qpart, nsplit, Q, full, ctl,
+                              timeout_ns, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
@@ -253,13 +257,13 @@ static cudaError_t gram_launch(bool fp64, int64_t nrows, int32_t n, const void* 
 }
 
 cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
-                       double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
-    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 0, s);
+                       double* Qpart, int32_t nsplit, double* Q, Control* ctl, uint64_t timeout_ns, cudaStream_t s) {
+    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 0, ctl, timeout_ns, s);
 }
 
 cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
-                      double* Qpart, int32_t nsplit, double* Q, cudaStream_t s) {
-    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 1, s);
+                      double* Qpart, int32_t nsplit, double* Q, Control* ctl, uint64_t timeout_ns, cudaStream_t s) {
+    return gram_launch(fp64, nrows, n, A, lda, B, ldb, Qpart, nsplit, Q, 1, ctl, timeout_ns, s);
 }
 
 cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C, const double* gamma, void* M,

@@ -92,8 +92,11 @@ cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
 
 // Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,
 // partials in double; then Q = sum of the partials in a fixed order.
+// FP32 operands run on tcgen05 (gram_tc05) when both arrays are TMA-aligned, else on mma.sync
+// (gram_tc); ctl and timeout_ns bound the waits of the tcgen05 kernel.
 cudaError_t gram_upper(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B,
-                       int64_t ldb, double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
+                       int64_t ldb, double* Qpart, int32_t nsplit, double* Q, Control* ctl, uint64_t timeout_ns,
+                       cudaStream_t s);
 int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
 // FP32 operands: the partial Grams on tensor cores (three BF16 pieces per operand, six products,
 // 32-row stages folded into FP32 and every 512 rows into FP64); Qpart as for gram_upper.  At most
@@ -101,9 +104,16 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
 // *used receives the count, the number of partial Grams written.
 cudaError_t gram_tc(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
                     double* Qpart, int32_t nsplit, int full, cudaStream_t s, int32_t* used);
+// The same partial Grams on tcgen05: 128 x 128 tiles, one CTA per SM, the same three-piece BF16
+// products, each 32-row stage added into a double-FP32 running sum in TMEM.  Returns
+// cudaErrorNotSupported (nothing launched) when A or B cannot be described by a TMA tensor map
+// (16-byte aligned base and stride).
+cudaError_t gram_tc05(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
+                      double* Qpart, int32_t nsplit, int full, Control* ctl, uint64_t timeout_ns, cudaStream_t s,
+                      int32_t* used);
 // Full Gram P[k][m] = sum_j A[j,k] B[j,m] (every k, m), same splitting and fixed-order reduction.
 cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
-                      double* Qpart, int32_t nsplit, double* Q, cudaStream_t s);
+                      double* Qpart, int32_t nsplit, double* Q, Control* ctl, uint64_t timeout_ns, cudaStream_t s);
 
 // Refinement helpers (FP32 storage):
 //   gram_comp:       P[k][m] = sum_j A[j,k] B[j,m] (every k, m; row-major) with exact

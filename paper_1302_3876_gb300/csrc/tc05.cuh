@@ -1,0 +1,170 @@
+// Blackwell (sm_103a) building blocks shared by the tcgen05 kernels of libenkf_ism:
+// mbarrier waits with an iteration and wall-clock bound, shared-memory matrix and
+// instruction descriptors of tcgen05.mma kind::f16 (BF16 operands, FP32 accumulator,
+// both operands K-major, no swizzle), the MMA issue and commit, TMEM loads and stores,
+// and the tiled tensor maps of the TMA copies.  No arithmetic of the filter lives here.
+//
+// Operand layout (K-major canonical, no swizzle): core matrices of 8 rows x 16 bytes
+// (8 BF16 along K); the two core matrices of one K-step of 16 lie 128 bytes apart (LBO)
+// and consecutive 8-row groups 256 bytes apart (SBO), so one K-step of R rows takes
+// R x 32 bytes and row r, K-group kg starts at (r / 8) * 256 + (r % 8) * 16 + kg * 128.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace enkf {
+namespace tc05 {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Releases a shared-memory slot that was read with ordinary loads and that a TMA copy (async
+// proxy) refills next: the proxy fence orders those reads before the copy's writes.  Without
+// it a copy issued as soon as the barrier completes can overwrite data whose loads are
+// still in flight (observed as whole operand rows taken from the next chunk).
+__device__ __forceinline__ void release_to_async(uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_arrive(bar);
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity`.  Returns false once it gives up (the CTA flag
+// *err is set and ENKF_ERR_TIMEOUT latched) or once another role of the CTA has.
+__device__ inline bool mbar_wait(uint64_t* bar, unsigned parity, int* err, Control* ctl, uint64_t timeout_ns) {
+    const uint64_t t0 = global_timer_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*(volatile int*)err) return false;
+            if (global_timer_ns() - t0 > timeout_ns || it > (1u << 26)) {
+                *(volatile int*)err = 1;
+                set_status(ctl, kErrTimeout);
+                return false;
+            }
+        }
+    }
+}
+// Wait bounded by time only (draining copies or MMAs after an error).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try(bar, parity) && global_timer_ns() - t0 < timeout_ns) {
+    }
+}
+
+// Shared-memory matrix descriptor: start >> 4 [0,14), leading byte offset >> 4 [16,30),
+// stride byte offset >> 4 [32,46), descriptor version 1 at [46,48), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t a = (smem_u32(p) >> 4) & 0x3FFFu;
+    return a | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator [4,6), BF16 A [7,10) and B [10,13),
+// both K-major, N >> 3 at [17,23), M >> 4 at [24,29).
+__device__ __forceinline__ unsigned instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] B[smem]; acc = 0 starts the accumulator from zero.
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Arrives once on `bar` when every MMA issued before it by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(unsigned* dst_smem, unsigned cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(dst_smem)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane (warp w reads lanes 32 (w % 4)..).
+__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+}
+__device__ __forceinline__ void tmem_st16(unsigned addr, const unsigned* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+            addr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// The registers a tcgen05.ld writes are valid only after tcgen05.wait::ld, but an asm
+// statement without operands does not order the arithmetic that reads them.  These forms
+// make the wait (and, for further arrays, an empty statement after it) redefine the
+// registers, so no use of them can be scheduled above the wait.
+__device__ __forceinline__ void tmem_wait_ld(unsigned* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void reg_fence16(unsigned* r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// TMA copy of one box of a 2-D tensor map into shared memory; completes `bar`'s transaction.
+// x (the inner coordinate) must be a multiple of 16 bytes of elements.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace tc05
+
+// Tiled FP32 tensor map of an inner x outer column-major array (inner contiguous, stride ld
+// elements between outer indices), box box_inner x box_outer, zero fill past the ends.
+// False if the base or the stride is not 16-byte aligned or the driver entry point is
+// unavailable.  swizzle128: the 128-byte swizzle (box_inner x 4 must then be 128).
+bool encode_f32_2d(CUtensorMap* map, const float* base, int64_t inner, int64_t outer, int64_t ld, int box_inner,
+                   int box_outer, bool swizzle128);
+
+}  // namespace enkf

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc05.cuh"
 
 namespace enkf {
 namespace {
@@ -45,27 +46,6 @@ constexpr int kMaxSmem = 232448;
 
 __host__ __device__ constexpr int b_chunk_bytes(int nb) { return 2 * nb * XKC * 2; }   // B hi + lo of one chunk
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 struct XaShared {
     uint64_t raw_full[XRS], raw_empty[XRS], a_full[4], a_empty[4], acc_full[2], acc_empty[2], drained;
     uint64_t xb_full[XBS], xb_empty[XBS];
@@ -73,65 +53,28 @@ struct XaShared {
     int err;
 };
 
-// Bounded wait for the phase of `parity`; false (CTA error flag and device status
-// latched) once it gives up or another role already has.
-__device__ bool mbar_wait(uint64_t* bar, unsigned parity, XaShared* sh, Control* ctl, uint64_t timeout_ns) {
-    const uint64_t t0 = global_timer_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0) {
-            if (*(volatile int*)&sh->err) return false;
-            if (global_timer_ns() - t0 > timeout_ns || it > (1u << 26)) {
-                *(volatile int*)&sh->err = 1;
-                set_status(ctl, kErrTimeout);
-                return false;
-            }
-        }
-    }
-}
-// Wait bounded by time only (draining after an error).
-__device__ void mbar_drain(uint64_t* bar, unsigned parity, uint64_t timeout_ns) {
-    const uint64_t t0 = global_timer_ns();
-    while (!mbar_try(bar, parity) && global_timer_ns() - t0 < timeout_ns) {
-    }
-}
+using tc05::fence_after;
+using tc05::fence_before;
+using tc05::mbar_arrive;
+using tc05::mbar_drain;
+using tc05::mbar_expect_tx;
+using tc05::mbar_init;
+using tc05::smem_u32;
+using tc05::tmem_ld16;
+using tc05::tmem_wait_ld;
 
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
-    // tcgen05 shared-memory matrix descriptor: start >> 4 [0,14), leading byte offset >> 4
-    // [16,30) (between core matrices along K), stride byte offset >> 4 [32,46) (between
-    // 8-row groups), descriptor version 1 at [46,48), no swizzle.
-    const uint64_t a = (smem_u32(p) >> 4) & 0x3FFFu;
-    return a | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, XaShared* sh, Control* ctl,
+                                          uint64_t timeout_ns) {
+    return tc05::mbar_wait(bar, parity, &sh->err, ctl, timeout_ns);
 }
-
-// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
-// N >> 3 at [17,23), M >> 4 at [24,29).
-__device__ __forceinline__ unsigned instr_desc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(XM >> 4) << 24);
+__device__ __forceinline__ uint64_t smem_desc(const void* p) { return tc05::smem_desc(p); }
+__device__ __forceinline__ unsigned instr_desc(int n) { return tc05::instr_desc(XM, n); }
+__device__ __forceinline__ void mma_bf16(unsigned d, uint64_t a, uint64_t b, unsigned idesc, int acc) {
+    tc05::mma_bf16(d, a, b, idesc, acc);
 }
-
-__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, unsigned idesc, int acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(addr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void mma_commit(uint64_t* bar) { tc05::mma_commit(bar); }
+__device__ __forceinline__ void tc_fence_before() { fence_before(); }
+__device__ __forceinline__ void tc_fence_after() { fence_after(); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -261,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                     const float* rw = reinterpret_cast<const float*>(raw + rs * kRawBytes);
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] = rw[(kh * 16 + q) * XM + r];
-                    mbar_arrive(&sh->raw_empty[rs]);
+                    tc05::release_to_async(&sh->raw_empty[rs]);
                 } else {
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
@@ -321,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                         float xb[16];
 #pragma unroll
                         for (int q = 0; q < 16; ++q) xb[q] = xs[(h * 16 + q) * XM];
-                        tmem_wait_ld();
+                        tmem_wait_ld(acc);
                         const int e0 = (gq + h) * 16;
                         if (i < p.nstate) {
 #pragma unroll
@@ -329,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                                 if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
                         }
                     }
-                    mbar_arrive(&sh->xb_empty[c]);
+                    tc05::release_to_async(&sh->xb_empty[c]);
                 }
                 if (!ok) break;
                 tc_fence_before();
@@ -350,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                 if (gq + 1 < g1) load_xb(i, gq + 1, xnext);
                 unsigned acc[16];
                 tmem_ld16(row_addr + gq * 16, acc);
-                tmem_wait_ld();
+                tmem_wait_ld(acc);
                 const int e0 = yb * nb + gq * 16;
                 if (i < p.nstate) {
 #pragma unroll
@@ -490,11 +433,11 @@ XaGeom xa_geom(int32_t nens, bool xbt) {
     return g;
 }
 
-// Tiled FP32 tensor map of an nstate x nens column-major array (rows inner), box 128 rows x
-// 32 members, zero fill past the ends; false if the base or stride is not 16-byte aligned or
-// the driver entry point is unavailable.
-bool encode_rows_members(CUtensorMap* map, const float* base, int64_t nstate, int32_t nens, int64_t ld) {
-    if ((uintptr_t)base % 16 != 0 || (ld * 4) % 16 != 0) return false;
+}  // namespace
+
+bool encode_f32_2d(CUtensorMap* map, const float* base, int64_t inner, int64_t outer, int64_t ld, int box_inner,
+                   int box_outer, bool swizzle128) {
+    if ((uintptr_t)base % 16 != 0 || (ld * 4) % 16 != 0 || inner >= (int64_t(1) << 31)) return false;
     // resolved through the runtime so the library has no link-time dependency on libcuda
     using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -509,16 +452,14 @@ bool encode_rows_members(CUtensorMap* map, const float* base, int64_t nstate, in
             encode = reinterpret_cast<EncodeTiled>(f);
     }
     if (!encode) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)nstate, (cuuint64_t)nens};
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    const cuuint32_t box[2] = {XM, XKC};
+    const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     const cuuint32_t estr[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-}  // namespace
 
 size_t xa_split_bytes(int32_t nens) {
     const XaGeom g = xa_geom(nens, false);
@@ -546,8 +487,9 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     CUtensorMap tmap, tmapb;
     memset(&tmap, 0, sizeof(tmap));
     memset(&tmapb, 0, sizeof(tmapb));
-    const bool tma = nstate < (int64_t(1) << 31) && encode_rows_members(&tmap, dXB, nstate, nens, ldx);
-    bool xbt = tma && g.nblocks == 1 && g.nchunks <= XBS && g.resident && encode_rows_members(&tmapb, XB, nstate, nens, ldb);
+    const bool tma = encode_f32_2d(&tmap, dXB, nstate, nens, ldx, XM, XKC, false);
+    bool xbt = tma && g.nblocks == 1 && g.nchunks <= XBS && g.resident &&
+               encode_f32_2d(&tmapb, XB, nstate, nens, ldb, XM, XKC, false);
     if (xbt) {
         const XaGeom gx = xa_geom(nens, true);
         if (gx.nas >= 2) g = gx;
