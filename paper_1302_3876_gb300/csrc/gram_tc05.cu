@@ -5,10 +5,13 @@
 // so both give the same products; here they run as tcgen05.mma (M = N = 128, K = 16)
 // with FP32 accumulators in TMEM.
 //
-// Tensor-core accumulation truncates, so every 32-row chunk is a stage of its own: its
-// twelve MMAs start from zero in one of two TMEM accumulators, and the epilogue adds the
-// stage into a double-FP32 running sum (TwoSum: hi + lo) that also lives in TMEM.  TMEM
-// columns: [0,128) and [128,256) the stage accumulators, [256,384) hi, [384,512) lo.
+// Tensor-core accumulation truncates, so the rows are summed in stages of stage_chunks
+// 32-row chunks (12 MMAs per chunk): a stage starts from zero in one of two TMEM
+// accumulators, and the epilogue adds it into a double-FP32 running sum (TwoSum: hi + lo)
+// that also lives in TMEM.  The truncation error grows with the stage length (relative
+// error of Q about 1.8e-7 with one chunk per stage, 8e-7 with four), and the fold is most
+// of the kernel's instructions.  TMEM columns: [0,128) and [128,256) the stage
+// accumulators, [256,384) hi, [384,512) lo.
 //
 // CTA: one 128 x 128 tile (kb, mb) of Q over a slice of the rows (blockIdx.y), one CTA per
 // SM, warp-specialised:
@@ -35,7 +38,7 @@ namespace {
 using namespace tc05;
 
 constexpr int GM = 128;                       // tile edge: MMA M = N = 128 members
-constexpr int GK = 32;                        // rows per chunk (two K-steps) = one stage
+constexpr int GK = 32;                        // rows per chunk (two K-steps)
 constexpr int GRS = 3;                        // raw stages
 constexpr int GPS = 2;                        // piece stages
 constexpr int kEpi = 256, kConv = 256;
@@ -57,7 +60,7 @@ constexpr int kSmem = 1024 + GRS * kRawBytes + GPS * kPieceBytes + (int)sizeof(G
 
 struct GramParams {
     int64_t nrows, rows_per_split;
-    int n, nt, full;
+    int n, nt, full, stage_chunks;
     double* Qpart;
     Control* ctl;
     uint64_t timeout_ns;
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
     const int64_t j0 = (int64_t)blockIdx.y * p.rows_per_split;
     const int64_t j1 = min(j0 + p.rows_per_split, p.nrows);
     const int nchunks = j1 > j0 ? (int)((j1 - j0 + GK - 1) / GK) : 0;
+    const int nstages = (nchunks + p.stage_chunks - 1) / p.stage_chunks;
 
     if (tid == 0) {
         for (int q = 0; q < GRS; ++q) mbar_init(&sh->raw_full[q], 1), mbar_init(&sh->raw_empty[q], kConv);
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
         const int quarter = warp & 3, half = warp >> 2;
         const unsigned lanes = tbase + ((unsigned)(quarter * 32) << 16);
         bool ok = true;
-        for (int g = 0; ok && g < nchunks; ++g) {
+        for (int g = 0; ok && g < nstages; ++g) {   // g: stage
             const int b = g & 1;
             if (!mbar_wait(&sh->acc_full[b], (unsigned)((g >> 1) & 1), &sh->err, p.ctl, p.timeout_ns)) {
                 ok = false;
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
             for (int c16 = 0; c16 < 4; ++c16) {
                 const unsigned col = (unsigned)(half * 64 + c16 * 16);
                 unsigned hi[16], lo[16];
-                if (nchunks > 0) {
+                if (nstages > 0) {
                     tmem_ld16(lanes + 256u + col, hi);
                     tmem_ld16(lanes + 384u + col, lo);
                     tmem_wait_ld(hi);
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
                     const int m = mb * GM + (int)col + q;
                     if (k < p.n && m < p.n && (p.full || k < m))
                         out[(int64_t)k * p.n + m] =
-                            nchunks > 0 ? (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]) : 0.0;
+                            nstages > 0 ? (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]) : 0.0;
                 }
             }
         }
@@ -237,9 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
             // products a_i b_j, i + j < 3, smallest first
             const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
             for (int g = 0; g < nchunks; ++g) {
-                const int b = g & 1, s = g % GPS;
-                if (g >= 2 &&
-                    !mbar_wait(&sh->acc_empty[b], (unsigned)(((g >> 1) - 1) & 1), &sh->err, p.ctl, p.timeout_ns))
+                const int st = g / p.stage_chunks, first = (g % p.stage_chunks) == 0;
+                const int b = st & 1, s = g % GPS;
+                if (first && st >= 2 &&
+                    !mbar_wait(&sh->acc_empty[b], (unsigned)(((st >> 1) - 1) & 1), &sh->err, p.ctl, p.timeout_ns))
                     break;
                 if (!mbar_wait(&sh->pc_full[s], (unsigned)((g / GPS) & 1), &sh->err, p.ctl, p.timeout_ns)) break;
                 fence_after();
@@ -251,9 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
 #pragma unroll
                     for (int q = 0; q < 6; ++q)
                         mma_bf16(d, smem_desc(pa0 + pa[q] * kPieceOp + ks * kStepBytes),
-                                 smem_desc(pb0 + pb[q] * kPieceOp + ks * kStepBytes), idesc, (ks | q) != 0);
+                                 smem_desc(pb0 + pb[q] * kPieceOp + ks * kStepBytes), idesc, !first || (ks | q) != 0);
                 mma_commit(&sh->pc_empty[s]);
-                mma_commit(&sh->acc_full[b]);
+                if (g % p.stage_chunks == p.stage_chunks - 1 || g == nchunks - 1) mma_commit(&sh->acc_full[b]);
             }
             // the commit arrives once every MMA issued above has completed
             mma_commit(&sh->drained);
@@ -272,8 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
 }  // namespace
 
 cudaError_t gram_tc05(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
-                      double* Qpart, int32_t nsplit, int full, Control* ctl, uint64_t timeout_ns, cudaStream_t s,
-                      int32_t* used) {
+                      double* Qpart, int32_t nsplit, int full, int stage_chunks, Control* ctl, uint64_t timeout_ns,
+                      cudaStream_t s, int32_t* used) {
     CUtensorMap tmA, tmB;
     memset(&tmA, 0, sizeof(tmA));
     memset(&tmB, 0, sizeof(tmB));
@@ -301,6 +306,7 @@ cudaError_t gram_tc05(int64_t nrows, int32_t n, const float* A, int64_t lda, con
     p.n = n;
     p.nt = nt;
     p.full = full;
+    p.stage_chunks = stage_chunks < 1 ? 1 : stage_chunks;
     p.Qpart = Qpart;
     p.ctl = ctl;
     p.timeout_ns = timeout_ns;

@@ -105,12 +105,13 @@ int32_t gram_upper_nsplit(int64_t nrows, int32_t n);
 cudaError_t gram_tc(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
                     double* Qpart, int32_t nsplit, int full, cudaStream_t s, int32_t* used);
 // The same partial Grams on tcgen05: 128 x 128 tiles, one CTA per SM, the same three-piece BF16
-// products, each 32-row stage added into a double-FP32 running sum in TMEM.  Returns
+// products, each stage of 32 * stage_chunks rows added into a double-FP32 running sum in TMEM
+// (the relative error grows with the stage: ~1.8e-7 for one chunk, ~8e-7 for four).  Returns
 // cudaErrorNotSupported (nothing launched) when A or B cannot be described by a TMA tensor map
 // (16-byte aligned base and stride).
 cudaError_t gram_tc05(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
-                      double* Qpart, int32_t nsplit, int full, Control* ctl, uint64_t timeout_ns, cudaStream_t s,
-                      int32_t* used);
+                      double* Qpart, int32_t nsplit, int full, int stage_chunks, Control* ctl, uint64_t timeout_ns,
+                      cudaStream_t s, int32_t* used);
 // Full Gram P[k][m] = sum_j A[j,k] B[j,m] (every k, m), same splitting and fixed-order reduction.
 cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_t lda, const void* B, int64_t ldb,
                       double* Qpart, int32_t nsplit, double* Q, Control* ctl, uint64_t timeout_ns, cudaStream_t s);
