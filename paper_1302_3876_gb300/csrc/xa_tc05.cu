@@ -14,9 +14,10 @@
 //               chunk marks its accumulator full.  Two accumulators in TMEM.
 //   warps 0-7   epilogue: warp w reads TMEM lanes 32 (w % 4).. (its 32 rows) for one
 //               half of the columns; X_A = X_B + acc with coalesced column accesses.
-//   warp 18     X_B loader (Nens <= 128 and a TMA-aligned X_B): TMA copies of the tile's
-//               X_B chunks into a ring the epilogue reads, so the epilogue waits on no
-//               global load; each half of the epilogue then takes whole 32-member chunks.
+//   warp 18     X_B loader (a TMA-aligned X_B): TMA copies of the column block's X_B
+//               chunks (128 rows x 32 members) of every tile, in order, into a four-slot
+//               ring the epilogue reads, so the epilogue waits on no global load; the two
+//               halves of the epilogue then take alternate chunks (one consumer per fill).
 // M is pre-split into hi/lo images of the same layout; they stay in shared memory for
 // the whole launch when they fit (Nens <= 128), else each chunk's part travels in the
 // operand slot.  Every mbarrier wait is bounded (iteration count and %globaltimer); on
@@ -230,12 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
         // ---------------- epilogue
         const int quarter = warp & 3, half = warp >> 2;
         const int ngroups = nb / 16;
-        int g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
-        if (p.xbt) {   // whole chunks (two groups of 16 members) per half: one consumer per X_B slot
-            const int hc = (nchunks + 1) / 2;
-            g0 = half ? 2 * hc : 0;
-            g1 = half ? ngroups : min(ngroups, 2 * hc);
-        }
+        const int g0 = half ? (ngroups + 1) / 2 : 0, g1 = half ? ngroups : (ngroups + 1) / 2;
+        const int nxc = (ngroups + 1) / 2;   // X_B chunks of a tile (two groups of 16 members each)
         int64_t t = 0;
         auto load_xb = [&](int64_t i, int gq, float* xb) {
             const int e0 = yb * nb + gq * 16;
@@ -251,28 +248,31 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                 tc_fence_after();
                 const unsigned row_addr = tbase + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * nb);
                 bool ok = true;
-                for (int gq = g0; gq < g1; gq += 2) {
-                    const int c = gq >> 1;   // X_B chunk: members 32 c .. 32 c + 31, [member][row]
-                    if (!mbar_wait(&sh->xb_full[c], (unsigned)(t & 1), sh, p.ctl, p.timeout_ns)) {
+                for (int c = half; c < nxc; c += 2) {
+                    // X_B chunk c: members yb nb + 32 c .., [member][row]; ring fill G
+                    const int64_t G = t * nxc + c;
+                    const int slot = (int)(G % XBS);
+                    if (!mbar_wait(&sh->xb_full[slot], (unsigned)((G / XBS) & 1), sh, p.ctl, p.timeout_ns)) {
                         ok = false;
                         break;
                     }
-                    const float* xs = reinterpret_cast<const float*>(xbs + c * kRawBytes) + quarter * 32 + lane;
-                    for (int h = 0; h < 2 && gq + h < g1; ++h) {
+                    const float* xs = reinterpret_cast<const float*>(xbs + slot * kRawBytes) + quarter * 32 + lane;
+                    for (int h = 0; h < 2 && 2 * c + h < ngroups; ++h) {
+                        const int gq = 2 * c + h;
                         unsigned acc[16];
-                        tmem_ld16(row_addr + (gq + h) * 16, acc);
+                        tmem_ld16(row_addr + gq * 16, acc);
                         float xb[16];
 #pragma unroll
                         for (int q = 0; q < 16; ++q) xb[q] = xs[(h * 16 + q) * XM];
                         tmem_wait_ld(acc);
-                        const int e0 = (gq + h) * 16;
+                        const int e0 = yb * nb + gq * 16;
                         if (i < p.nstate) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q)
                                 if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
                         }
                     }
-                    tc05::release_to_async(&sh->xb_empty[c]);
+                    tc05::release_to_async(&sh->xb_empty[slot]);
                 }
                 if (!ok) break;
                 tc_fence_before();
@@ -305,32 +305,27 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
             mbar_arrive(&sh->acc_empty[b]);
         }
     } else if (warp == 18) {
-        // ---------------- X_B loader (TMA): chunk c of each tile into slot c
+        // ---------------- X_B loader (TMA): fill G = (tile count) x nxc + c into slot G % XBS
         if (TMA && p.xbt && lane == 0) {
-            int64_t t = 0;
-            int cstop = -1;   // chunk whose slot wait gave up (tile t); -1: every tile issued
-            for (int64_t tile = blockIdx.x; cstop < 0 && tile < ntiles; tile += gridDim.x, ++t) {
-                for (int c = 0; c < nchunks; ++c) {
-                    if (t >= 1 && !mbar_wait(&sh->xb_empty[c], (unsigned)((t - 1) & 1), sh, p.ctl, p.timeout_ns)) {
-                        cstop = c;
+            const int nxc = (nb / 16 + 1) / 2;
+            int64_t G = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int c = 0; c < nxc; ++c, ++G) {
+                    const int slot = (int)(G % XBS);
+                    if (G >= XBS && !mbar_wait(&sh->xb_empty[slot], (unsigned)((G / XBS - 1) & 1), sh, p.ctl,
+                                               p.timeout_ns)) {
+                        ok = false;
                         break;
                     }
-                    mbar_expect_tx(&sh->xb_full[c], kRawBytes);
-                    const int x = (int)(tile * XM), y = c * XKC;
-                    asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
-                        "{%2, %3}], [%4];\n" ::"r"(smem_u32(xbs + c * kRawBytes)),
-                        "l"(reinterpret_cast<uint64_t>(&tmapb)), "r"(x), "r"(y), "r"(smem_u32(&sh->xb_full[c]))
-                        : "memory");
+                    mbar_expect_tx(&sh->xb_full[slot], kRawBytes);
+                    tc05::tma_load_2d(xbs + slot * kRawBytes, &tmapb, (int)(tile * XM), yb * nb + c * XKC,
+                                      &sh->xb_full[slot]);
                 }
             }
-            // every issued copy has landed before the CTA may exit: the last fill of slot c was
-            // tile t - 1, or tile t for the slots filled before the wait gave up
-            if (cstop >= 0) --t;   // back to the tile that stopped (its loop increment ran)
-            for (int c = 0; c < nchunks; ++c) {
-                const int64_t last = (cstop >= 0 && c < cstop) ? t : t - 1;
-                if (last >= 0) mbar_drain(&sh->xb_full[c], (unsigned)(last & 1), p.timeout_ns);
-            }
+            // every issued copy has landed before the CTA may exit (the last fill of each slot)
+            for (int64_t f = G - 1; f >= 0 && f >= G - XBS; --f)
+                mbar_drain(&sh->xb_full[f % XBS], (unsigned)((f / XBS) & 1), p.timeout_ns);
         }
     } else {
         // ---------------- MMA issue (warp 17, one thread)
@@ -482,14 +477,13 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     }
     // TMA tensor maps of dX_B and X_B (rows inner, members outer), box 128 rows x 32 members;
     // the rows and members past the end read as zeros.  Each needs a 16-byte aligned base and
-    // stride; X_B goes through TMA only for a single column block of at most four chunks whose
-    // M images stay resident (Nens <= 128), else the epilogue loads it from global memory.
+    // stride; with an unaligned X_B (or no room for its ring) the epilogue loads it from global
+    // memory.
     CUtensorMap tmap, tmapb;
     memset(&tmap, 0, sizeof(tmap));
     memset(&tmapb, 0, sizeof(tmapb));
     const bool tma = encode_f32_2d(&tmap, dXB, nstate, nens, ldx, XM, XKC, false);
-    bool xbt = tma && g.nblocks == 1 && g.nchunks <= XBS && g.resident &&
-               encode_f32_2d(&tmapb, XB, nstate, nens, ldb, XM, XKC, false);
+    bool xbt = tma && encode_f32_2d(&tmapb, XB, nstate, nens, ldb, XM, XKC, false);
     if (xbt) {
         const XaGeom gx = xa_geom(nens, true);
         if (gx.nas >= 2) g = gx;
