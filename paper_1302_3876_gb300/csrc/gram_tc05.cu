@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
         // ---------------- epilogue: stage sums into hi + lo (TwoSum), then the partial Gram
         const int quarter = warp & 3, half = warp >> 2;
         const unsigned lanes = tbase + ((unsigned)(quarter * 32) << 16);
+        // strict upper triangle of a diagonal tile: column groups left of this warp's 32 rows
+        // (every m < every k) are not needed -- 12 of the 32 groups
+        const int cskip = (!p.full && kb == mb) ? quarter * 32 : 0;
         bool ok = true;
         for (int g = 0; ok && g < nstages; ++g) {   // g: stage
             const int b = g & 1;
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
 #pragma unroll 1
             for (int c16 = 0; c16 < 4; ++c16) {
                 const unsigned col = (unsigned)(half * 64 + c16 * 16);
+                if ((int)col + 16 <= cskip) continue;
                 unsigned acc[16], hi[16], lo[16];
                 tmem_ld16(lanes + (unsigned)(b * GM) + col, acc);
                 if (g > 0) {
@@ -218,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc05_kernel(const __grid_con
 #pragma unroll 1
             for (int c16 = 0; c16 < 4; ++c16) {
                 const unsigned col = (unsigned)(half * 64 + c16 * 16);
+                if ((int)col + 16 <= cskip) continue;
                 unsigned hi[16], lo[16];
                 if (nstages > 0) {
                     tmem_ld16(lanes + 256u + col, hi);
