@@ -304,13 +304,11 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
         stage(0, 0);
         for (int tile = 0; tile < ntiles; ++tile) {
             const int buf = tile & 1;
-            if (tile + 1 < ntiles) {
-                stage(tile + 1, buf ^ 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            // this tile's copies (the only ones in flight) have landed; after the barrier every
+            // thread is also done with the other buffer, so the next tile is staged into it
+            cp_async_wait<0>();
             __syncthreads();
+            if (tile + 1 < ntiles) stage(tile + 1, buf ^ 1);
             float* xs = s.Xs + buf * CT * XLD;
             const float* ups = s.UPs + buf * kPB * RT;
             const float* vns = s.VNs + buf * kPB * RT;
@@ -365,7 +363,6 @@ __device__ void sweep_t(const PanelArgs& a, const PanelSmem& s, int64_t r0, int6
                                          fmaf(vv[s4].z, xv[q].z, fmaf(vv[s4].w, xv[q].w, acc[s4][q]))));
                 }
             }
-            __syncthreads();     // the buffer is refilled by the next iteration's prefetch
         }
         if (nb > 0) {
             // combine the two row halves in a fixed order, then write this CTA's partial
@@ -591,13 +588,11 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
         stage(0, 0);
         for (int tile = 0; tile < ntiles; ++tile) {
             const int buf = tile & 1;
-            if (tile + 1 < ntiles) {
-                stage(tile + 1, buf ^ 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            // this tile's copies (the only ones in flight) have landed; after the barrier every
+            // thread is also done with the other buffer, so the next tile is staged into it
+            cp_async_wait<0>();
             __syncthreads();
+            if (tile + 1 < ntiles) stage(tile + 1, buf ^ 1);
             float* xs = s.Xs + buf * CT * XLD;
             const float* ups = s.UPs + buf * kPB * RT;
             const float* vns = s.VNs + buf * kPB * RT;
@@ -739,7 +734,6 @@ __device__ void sweep_tc(const PanelArgs& a, const PanelSmem& s, int64_t r0, int
 #pragma unroll
                     for (int h = 0; h < 4; ++h) acc2[mt][h] += tile2[mt][h];
             }
-            __syncthreads();     // the buffers are refilled by the next iteration
         }
         if (nb > 0) {
 #pragma unroll
