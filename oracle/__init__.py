@@ -60,6 +60,13 @@ def _load():
                 "oracle_residual": ([i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp, i64], ctypes.c_int),
                 "oracle_l96_rhs": ([i64, vp, dbl, vp], None),
                 "oracle_l96_rk4": ([i64, i32, vp, i64, dbl, dbl, i32], ctypes.c_int),
+                "oracle_inflate": ([i64, i32, dbl, vp, i64], None),
+                "oracle_localized_increment_literal": ([i64, i64, i32, i32, i32, dbl, dbl, vp, i64, vp, i64, vp,
+                                                        i64, vp, i64], None),
+                "oracle_localized_update": ([i64, i64, i32, i32, i32, dbl, dbl, vp, i64, vp, i64, vp, i64, vp,
+                                             i64, vp, i64], ctypes.c_int),
+                "oracle_ism_step1_blockdiag": ([i64, i32, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp, i64],
+                                               ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -219,6 +226,78 @@ def analysis(r, V, D, XB, dXB):
     M = vtz(V, Z)
     XA = analysis_update(XB, dXB, M)
     return {"Z": Z, "gamma": gamma, "M": M, "XA": XA}
+
+
+# ---------------------------------------------------------------------------
+# Inflation, partial localization, block-diagonal R (Sec. 3.1.1, 3.1.2, 3.1)
+# ---------------------------------------------------------------------------
+
+def inflate(X, alpha):
+    """x_i <- xbar + alpha (x_i - xbar) for every member (Sec. 3.1.1); returns a new array."""
+    X = np.array(_f64(X, "X"), copy=True)
+    _load().oracle_inflate(X.shape[1], X.shape[0], float(alpha), _p(X), X.shape[1])
+    return X
+
+
+def _loc_args(length, radius):
+    return float(length), (-1.0 if radius is None else float(radius))
+
+
+def localized_increment_literal(dXB, V, Z, stride, length, radius=None):
+    """dX[i,l] = sum_k S[i,k] sum_j delta_ij V[j,k] Z[j,l] (eq. localized-correction-component),
+    as printed; tiny inputs only.  radius None = no cut-off.  Returns dX with shape (nrhs, nstate)."""
+    dXB, V, Z = _f64(dXB, "dXB"), _f64(V, "V"), _f64(Z, "Z")
+    nens, nstate = dXB.shape
+    nobs, nrhs = V.shape[1], Z.shape[0]
+    if (nobs - 1) * stride >= nstate:
+        raise ValueError("observation rows exceed the state")
+    L, rad = _loc_args(length, radius)
+    dX = np.zeros((nrhs, nstate))
+    _load().oracle_localized_increment_literal(nstate, nobs, nens, nrhs, stride, L, rad, _p(dXB), nstate, _p(V),
+                                               nobs, _p(Z), Z.shape[1], _p(dX), nstate)
+    return dX
+
+
+def localized_update(XB, dXB, V, Z, stride, length, radius=None):
+    """X_A = X_B + (Delta o (S V^T)) Z (Sec. 3.1.2, matrix form).  Returns X_A (nrhs, nstate)."""
+    XB, dXB, V, Z = _f64(XB, "XB"), _f64(dXB, "dXB"), _f64(V, "V"), _f64(Z, "Z")
+    nens, nstate = dXB.shape
+    nobs, nrhs = V.shape[1], Z.shape[0]
+    if (nobs - 1) * stride >= nstate:
+        raise ValueError("observation rows exceed the state")
+    L, rad = _loc_args(length, radius)
+    XA = np.zeros((nrhs, nstate))
+    st = _load().oracle_localized_update(nstate, nobs, nens, nrhs, stride, L, rad, _p(dXB), nstate, _p(V), nobs,
+                                         _p(Z), Z.shape[1], _p(XB), XB.shape[1], _p(XA), nstate)
+    if st != 0:
+        raise MemoryError("oracle_localized_update failed")
+    return XA
+
+
+def ism_step1_blockdiag(Rblk, V, D):
+    """Step 1 with block-diagonal R (Sec. 3.1): (U^(0), Z^(0)) = (R^{-1} V, R^{-1} D), R = diag(R_b).
+    Rblk has shape (nblk, bs, bs) (symmetric blocks; the last may be used in its leading part)."""
+    Rblk = np.ascontiguousarray(np.asarray(Rblk, dtype=np.float64))
+    V, D = _f64(V, "V"), _f64(D, "D")
+    nobs = V.shape[1]
+    nblk, bs, _ = Rblk.shape
+    if nblk != (nobs + bs - 1) // bs:
+        raise ValueError("block count does not cover nobs")
+    # (nblk, bs, bs) C-order = column-major blocks of a symmetric matrix either way
+    U = np.zeros((V.shape[0], nobs))
+    Z = np.zeros((D.shape[0], nobs))
+    st = _load().oracle_ism_step1_blockdiag(nobs, V.shape[0], D.shape[0], bs, _p(Rblk), _p(V), V.shape[1], _p(D),
+                                            D.shape[1], _p(U), nobs, _p(Z), nobs)
+    if st != 0:
+        raise FloatingPointError(f"block {-st - 1} of R is not positive definite")
+    return U, Z
+
+
+def ism_solve_blockdiag(Rblk, V, D, return_gamma=False):
+    """Z = (R + V V^T)^{-1} D for block-diagonal R: the block Step 1, then Step 2 unchanged."""
+    U, Z = ism_step1_blockdiag(Rblk, V, D)
+    gamma = ism_levels(V, U, Z)
+    return (Z, gamma) if return_gamma else Z
 
 
 # ---------------------------------------------------------------------------

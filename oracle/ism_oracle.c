@@ -252,3 +252,174 @@ int oracle_l96_rk4(int64_t nstate, int32_t nens, double* X, int64_t ld, double F
     }
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Inflation, localization and block-diagonal R (Sec. 3.1.1, 3.1.2, 3.1)    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Multiplicative inflation (Sec. 3.1.1, inflation aspects): every member is
+ * pushed away from the ensemble mean by the factor alpha,
+ *   x_i <- xbar + alpha (x_i - xbar),   1 <= i <= Nens,
+ * so the ensemble covariance grows by alpha^2.  In place on X (nstate x nens).
+ */
+void oracle_inflate(int64_t nstate, int32_t nens, double alpha, double* X, int64_t ld) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nstate; ++i) {
+        double s = 0.0;
+        for (int32_t e = 0; e < nens; ++e) s += X[e * ld + i];
+        double m = s / (double)nens;
+        for (int32_t e = 0; e < nens; ++e) X[e * ld + i] = m + alpha * (X[e * ld + i] - m);
+    }
+}
+
+/*
+ * Impact factor delta_{i,j} of observation j on state component i (Sec. 3.1.2,
+ * partial localization; the Lorenz-96 choice of Sec. 4.2 is length = Nstate and
+ * no cut-off): the distance d between state index i and the observed state index
+ * j * stride, taken on the periodic ring of nstate points, gives
+ *   delta = exp(-d / length)   when radius < 0 or d <= radius,
+ *   delta = 0                  outside the radius of influence.
+ */
+static double loc_delta(int64_t nstate, int32_t stride, double length, double radius, int64_t i, int64_t j) {
+    int64_t d = i - j * (int64_t)stride;
+    if (d < 0) d = -d;
+    if (nstate - d < d) d = nstate - d;
+    if (radius >= 0.0 && (double)d > radius) return 0.0;
+    return exp(-(double)d / length);
+}
+
+/*
+ * Partial localization, eq. (localized-correction-component), written out as
+ * printed: for every state component i and member l,
+ *   dX[i, l] = sum_k S[i, k] sum_j delta_{i,j} V[j, k] Z[j, l],
+ * with S = dX_B / sqrt(Nens - 1) (k over the nens members, j over the nobs
+ * observations; V is nobs x nens, so the paper's V_{k,j} is V[j, k] here).
+ * Costs Nstate * nrhs * Nens * Nobs products: tiny inputs only.  Writes the
+ * increment dX (nstate x nrhs, ld ldo).
+ */
+void oracle_localized_increment_literal(int64_t nstate, int64_t nobs, int32_t nens, int32_t nrhs, int32_t stride,
+                                        double length, double radius, const double* dXB, int64_t ldx,
+                                        const double* V, int64_t ldv, const double* Z, int64_t ldz,
+                                        double* dX, int64_t ldo) {
+    double scale = 1.0 / sqrt((double)(nens - 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nstate; ++i) {
+        for (int32_t l = 0; l < nrhs; ++l) {
+            double outer = 0.0;
+            for (int32_t k = 0; k < nens; ++k) {
+                double inner = 0.0;
+                for (int64_t j = 0; j < nobs; ++j)
+                    inner += loc_delta(nstate, stride, length, radius, i, j) * V[k * ldv + j] * Z[l * ldz + j];
+                outer += dXB[k * ldx + i] * scale * inner;
+            }
+            dX[l * ldo + i] = outer;
+        }
+    }
+}
+
+/*
+ * Partial localization in the matrix form the paper gives beside the component
+ * formula (Sec. 3.1.2):  dX = (Delta o (S V^T)) Z,  Delta = (delta_{i,j}) of size
+ * Nstate x Nobs, o the Schur product.  For each state row i: the row
+ * t_j = delta_{i,j} (S V^T)[i, j] over all observations j (sum over members in
+ * ascending order), then dX[i, l] = sum_j t_j Z[j, l] (ascending j), and
+ *   X_A = X_B + dX.
+ * XA may alias XB.
+ */
+int oracle_localized_update(int64_t nstate, int64_t nobs, int32_t nens, int32_t nrhs, int32_t stride, double length,
+                            double radius, const double* dXB, int64_t ldx, const double* V, int64_t ldv,
+                            const double* Z, int64_t ldz, const double* XB, int64_t ldb, double* XA, int64_t lda) {
+    double scale = 1.0 / sqrt((double)(nens - 1));
+    int status = 0;
+#pragma omp parallel
+    {
+        double* t = (double*)malloc(sizeof(double) * (size_t)(nobs > 0 ? nobs : 1));
+        if (!t) {
+#pragma omp atomic write
+            status = -1;
+        } else {
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < nstate; ++i) {
+                for (int64_t j = 0; j < nobs; ++j) {
+                    double sv = 0.0;
+                    for (int32_t k = 0; k < nens; ++k) sv += dXB[k * ldx + i] * scale * V[k * ldv + j];
+                    t[j] = loc_delta(nstate, stride, length, radius, i, j) * sv;
+                }
+                for (int32_t l = 0; l < nrhs; ++l) {
+                    double s = 0.0;
+                    for (int64_t j = 0; j < nobs; ++j) s += t[j] * Z[l * ldz + j];
+                    XA[l * lda + i] = XB[l * ldb + i] + s;
+                }
+            }
+            free(t);
+        }
+    }
+    return status;
+}
+
+/*
+ * Step 1 with a block-diagonal R (Sec. 3.1: R^{-1} = diag(R_b^{-1}) is applied
+ * block by block):  Z^(0) = R^{-1} D,  U^(0) = R^{-1} V.  Block b covers rows
+ * [b*bs, min(nobs, (b+1)*bs)) and is stored dense, column-major, in the leading
+ * m x m part of the bs x bs matrix at Rblk + b*bs*bs (m = rows of the block).
+ * Each block is factored R_b = L L^T (Cholesky) and every column is solved by
+ * forward then backward substitution.  Returns 0, or -(b+1) when block b is not
+ * positive definite.
+ */
+int oracle_ism_step1_blockdiag(int64_t nobs, int32_t nens, int32_t nrhs, int32_t bs, const double* Rblk,
+                               const double* V, int64_t ldv, const double* D, int64_t ldd, double* U, int64_t ldu,
+                               double* Z, int64_t ldz) {
+    int64_t nblk = (nobs + bs - 1) / bs;
+    int status = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t b = 0; b < nblk; ++b) {
+        int64_t r0 = b * bs;
+        int32_t m = (int32_t)((nobs - r0) < bs ? (nobs - r0) : bs);
+        const double* A = Rblk + b * (int64_t)bs * bs;
+        double* L = (double*)calloc((size_t)m * m, sizeof(double));
+        double* x = (double*)malloc(sizeof(double) * (size_t)m);
+        if (!L || !x) {
+            free(L);
+            free(x);
+#pragma omp atomic write
+            status = -1;
+            continue;
+        }
+        int ok = 1;
+        for (int32_t c = 0; c < m && ok; ++c) {
+            double s = A[c * bs + c];
+            for (int32_t p = 0; p < c; ++p) s -= L[p * m + c] * L[p * m + c];
+            if (!(s > 0.0)) { ok = 0; break; }
+            double lcc = sqrt(s);
+            L[c * m + c] = lcc;
+            for (int32_t q = c + 1; q < m; ++q) {
+                double t = A[c * bs + q];
+                for (int32_t p = 0; p < c; ++p) t -= L[p * m + q] * L[p * m + c];
+                L[c * m + q] = t / lcc;
+            }
+        }
+        if (!ok) {
+#pragma omp atomic write
+            status = (int)-(b + 1);
+        } else {
+            for (int32_t col = 0; col < nens + nrhs; ++col) {
+                const double* in = col < nens ? V + col * ldv + r0 : D + (col - nens) * ldd + r0;
+                double* out = col < nens ? U + col * ldu + r0 : Z + (col - nens) * ldz + r0;
+                for (int32_t q = 0; q < m; ++q) {          /* L y = rhs */
+                    double t = in[q];
+                    for (int32_t p = 0; p < q; ++p) t -= L[p * m + q] * x[p];
+                    x[q] = t / L[q * m + q];
+                }
+                for (int32_t q = m - 1; q >= 0; --q) {     /* L^T out = y */
+                    double t = x[q];
+                    for (int32_t p = q + 1; p < m; ++p) t -= L[q * m + p] * out[p];
+                    out[q] = t / L[q * m + q];
+                }
+            }
+        }
+        free(L);
+        free(x);
+    }
+    return status;
+}
