@@ -641,6 +641,138 @@ def run_lorenz_cycle(args):
                       "wall_s": time.perf_counter() - t0, "data": "synthetic"}), flush=True)
 
 
+def run_next_rows(args):
+    """The rows beside the analysis, each timed by CUDA events on its own and set against its roofline:
+    inflation fused into the prep (Nstate 2^21, every 4th variable observed, 128 members, FP32), partial
+    localization (the Lorenz-96 cycle size Nstate 4096 / Nobs 2048 / 256 members with the paper's weights
+    exp(-d / Nstate), and a 64-point cut-off at Nstate 2^21 / Nobs 2^19 / 128 members), the block-diagonal
+    R path (32 x 32 blocks at Nobs 2^19, 128 members: whitening, analysis with r = 1, unwhitening), and the
+    Lorenz-96 filter with inflation and localization against the unlocalized filter (analysis RMSE)."""
+    import torch
+    import synth
+    from paper_1302_3876_gb300 import cycle as C
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+    hbm, hbm_src = read_peaks()
+    fp32 = fp32_alu_peak_tflops()
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.seed_for("next_rows"))
+    k = max(3, min(args.steps, 50))
+    out = {}
+    part = args.next_part
+
+    if part in ("all", "inflate"):
+        nstate, nobs, nens, stride = NSTATE, NOBS, NENS, STRIDE
+        X = torch.randn(nens, nstate, device=dev, generator=gen) + 8.0
+        Y = torch.randn(nens, nobs, device=dev, generator=gen) + 8.0
+        dX, V, D = torch.empty_like(X), torch.empty(nens, nobs, device=dev), torch.empty(nens, nobs, device=dev)
+        fn = lambda: enkf.enkf_inflate_prep(stride, 1.01, X, V, dXB=dX, Y=Y, D=D)  # noqa: E731
+        for _ in range(args.warmup):
+            fn()
+        ms = _events_ms(fn, k)
+        nbytes = 4 * nens * (3 * nstate + 3 * nobs)    # X_B read and written, dX_B written; Y read, V and D written
+        out["inflate_prep"] = {"config": f"Nstate={nstate} Nobs={nobs} Nens={nens} FP32", "ms": ms,
+                               "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm,
+                                            "unit": "GB/s", "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                                            "peak_source": hbm_src, "bytes": nbytes}}
+        del X, Y, dX, V, D
+
+    if part in ("all", "localize"):
+        cases = [("lorenz_cycle_paper_weights", 4096, 2, 256, 4096.0, None, torch.float32),
+                 ("lorenz_cycle_paper_weights_fp64", 4096, 2, 256, 4096.0, None, torch.float64),
+                 ("large_cutoff64", NSTATE, STRIDE, NENS, 32.0, 64.0, torch.float32)]
+        for name, nstate, stride, nens, length, radius, dt in cases:
+            nobs = (nstate - 1) // stride + 1
+            dX = torch.randn(nens, nstate, device=dev, generator=gen, dtype=dt)
+            XB = dX + 8.0
+            V = torch.randn(nens, nobs, device=dev, generator=gen, dtype=dt) / math.sqrt(nens - 1)
+            Z = torch.randn(nens, nobs, device=dev, generator=gen, dtype=dt)
+            XA = torch.empty_like(XB)
+            fn = lambda: enkf.enkf_localized_update(stride, length, radius, dX, V, Z, XB, XA)  # noqa: E731
+            for _ in range(args.warmup):
+                fn()
+            ms = _events_ms(fn, k)
+            if radius is None:
+                pairs = nstate * nobs
+            else:
+                pairs = nobs * min(nstate, 2 * int(math.floor(radius)) + 1)
+            fl = 4 * nens * pairs                           # (S V^T) entry and its use in T Z: 2 N + 2 N flops
+            nbytes = (4 if dt == torch.float32 else 8) * nens * (3 * nstate + 2 * nobs)
+            peak = fp32 if dt == torch.float32 else None
+            out["localized_update_" + name] = {
+                "config": f"Nstate={nstate} Nobs={nobs} Nens={nens} length={length} radius={radius} "
+                          f"{'FP32' if dt == torch.float32 else 'FP64'}",
+                "ms": ms, "pairs": pairs, "gflop": fl / 1e9, "tflops": fl / (ms / 1e3) / 1e12,
+                "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": (fl / (ms / 1e3) / 1e12 / peak) if peak else None,
+                             "peak_source": "derived FP32 CUDA-core peak" if peak else None},
+                "hbm_gbs_compulsory": nbytes / (ms / 1e3) / 1e9}
+            del dX, XB, V, Z, XA
+
+    if part in ("all", "rblock"):
+        nstate, nobs, nens, bs = NSTATE, NOBS, NENS, 32
+        nblk = nobs // bs
+        A = torch.randn(nblk, bs, bs, device=dev, generator=gen, dtype=torch.float64)
+        R = A @ A.transpose(1, 2) / bs + torch.diag_embed(0.5 + torch.rand(nblk, bs, device=dev, generator=gen,
+                                                                             dtype=torch.float64))
+        L = torch.empty_like(R)
+        enkf.enkf_rblock_factor(nobs, bs, R, L)
+        dX = torch.randn(nens, nstate, device=dev, generator=gen)
+        D0 = torch.randn(nens, nobs, device=dev, generator=gen)
+        V, D, Z = torch.empty(nens, nobs, device=dev), torch.empty_like(D0), torch.empty_like(D0)
+        XA = torch.empty_like(dX)
+        ones = torch.ones(nobs, device=dev)
+        plan = enkf.Plan(nstate, nobs, nens, enkf.ENKF_PANEL_FP32, panel_b=32, device=dev)
+        phase = {}
+
+        def step():
+            plan.obs_prep(STRIDE, 0, None, dX, V)
+            D.copy_(D0)
+            enkf.enkf_rblock_whiten(bs, L, V, D)
+            plan.analysis(ones, V, D, dXB=dX, XB=dX, XA=XA, Z=Z)
+            enkf.enkf_rblock_unwhiten(bs, L, Z)
+
+        for _ in range(args.warmup):
+            step()
+        ms = _events_ms(step, k)
+        phase["whiten_ms"] = _events_ms(lambda: enkf.enkf_rblock_whiten(bs, L, V, D), k)
+        phase["unwhiten_ms"] = _events_ms(lambda: enkf.enkf_rblock_unwhiten(bs, L, Z), k)
+        plan.close()
+        nb_w = 4 * 4 * nobs * nens                          # V and D read and written
+        out["rblock_analysis"] = {
+            "config": f"Nstate={nstate} Nobs={nobs} Nens={nens} blocks {bs}x{bs}, panel FP32 analysis",
+            "ms_per_analysis": ms, "analyses_per_s": 1e3 / ms, **phase,
+            "whiten_roofline": {"bound": "hbm", "achieved": nb_w / (phase["whiten_ms"] / 1e3) / 1e9, "peak": hbm,
+                                "unit": "GB/s", "frac": nb_w / (phase["whiten_ms"] / 1e3) / 1e9 / hbm,
+                                "fp64_gflop": nobs * 2 * nens * bs / 1e9}}
+        del A, R, L, dX, D0, V, D, Z, XA
+
+    if part in ("all", "cycle"):
+        # partial localization leaves (R + V V^T)^{-1} unlocalized: with short correlation lengths the
+        # cycle diverges (the analysis then reports ENKF_ERR_NUMERIC), which is recorded, not raised
+        res = {}
+        for name, kw in (("rk4", {}),
+                         ("rk4_paper_localization", {"loc_length": 4096.0, "loc_radius": None}),
+                         ("rk4_paper_localization_inflation1.02", {"loc_length": 4096.0, "loc_radius": None,
+                                                                    "inflation": 1.02}),
+                         ("rk4_localization_length64_radius128_inflation1.05",
+                          {"loc_length": 64.0, "loc_radius": 128.0, "inflation": 1.05})):
+            cyc = C.LorenzCycle(4096, 256, **kw)
+            try:
+                rmse, cps, _ = cyc.run(args.cycles, "rk4")
+                res[name] = {"analysis_rmse": rmse, "cycles_per_s": cps}
+            except enkf.EnkfError as e:
+                torch.cuda.synchronize()
+                res[name] = {"numeric_error_in_cycle": cyc.cycle_index, "status": enkf.status_name(e.status)}
+            cyc.close()
+        out["lorenz_cycle"] = {"config": f"Nstate=4096 Nens=256 Nobs=2048, {args.cycles} cycles of 5 RK4 steps",
+                               "methods": res}
+
+    print(json.dumps({"workload": "next_rows", "rows": out, "steps": k, "warmup": args.warmup,
+                      "data": "synthetic"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -657,8 +789,11 @@ def main():
                          "path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
     ap.add_argument("--refine", action="store_true", help="one step of iterative refinement (panel modes)")
-    ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle"],
-                    default="large_single")
+    ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle",
+                                           "next_rows"], default="large_single")
+    ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "cycle"], default="all",
+                    help="next_rows workload: run one part only")
+    ap.add_argument("--cycles", type=int, default=200, help="next_rows workload: assimilation cycles per filter")
     ap.add_argument("--train-cycles", type=int, default=60)
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--scale-div", type=int, default=1,
@@ -672,6 +807,8 @@ def main():
         run_batch_local(args)
     elif args.workload == "lorenz_cycle":
         run_lorenz_cycle(args)
+    elif args.workload == "next_rows":
+        run_next_rows(args)
     else:
         run_ours(args)
 

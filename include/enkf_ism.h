@@ -288,6 +288,72 @@ ENKF_API enkf_status enkf_surrogate_train_step(float* master, float* adam_m, flo
                                                float* sq_err, float* grad, void* stream);
 
 /*
+ * enkf_inflate_prep -- multiplicative inflation fused into the centering observation
+ * prep (Sec. 3.1.1, inflation aspects: x_i <- xbar + alpha (x_i - xbar), which scales
+ * the ensemble covariance by alpha^2; then the prep of enkf_obs_prep with center = 1).
+ * One pass over X_B:
+ *   XB   nstate x nens, ld ldb, in/out: overwritten by the inflated ensemble.
+ *   dXB  nstate x nens, ld ldx, output (nullable): deviations of the inflated ensemble
+ *        from the mean (the mean is unchanged by inflation).
+ *   V    nobs x nens, ld ldv, output: H dX_B / sqrt(Nens - 1), H = rows 0, obs_stride, ...
+ *   Y, D nobs x nens (both or neither): D = Y - H X_B of the inflated ensemble.
+ * precision ENKF_FP64 or ENKF_FP32 (element type of every array); alpha >= 0 (1 = no
+ * inflation); nens >= 2; (nobs - 1) * obs_stride < nstate.  Means in FP64.
+ */
+ENKF_API enkf_status enkf_inflate_prep(int64_t nstate, int64_t nobs, int32_t nens, int32_t precision,
+                                       int32_t obs_stride, double alpha, void* XB, int64_t ldb, void* dXB,
+                                       int64_t ldx, const void* Y, int64_t ldy, void* V, int64_t ldv, void* D,
+                                       int64_t ldd, void* stream);
+
+/*
+ * enkf_localized_update -- partial localization of the analysis increment (Sec. 3.1.2,
+ * eq. localized-correction-component and its matrix form):
+ *   X_A = X_B + (Delta o (S V^T)) Z,   S = dX_B / sqrt(Nens - 1),
+ *   dX_A[i, l] = sum_k S[i, k] sum_j delta_ij V[j, k] Z[j, l],
+ * with delta_ij = exp(-d / length) when radius < 0 or d <= radius, else 0, and d the
+ * periodic distance between state index i and the observed state index j * obs_stride
+ * on the ring of nstate points (the Lorenz-96 weights of Sec. 4.2 are length = nstate,
+ * no cut-off).  It replaces the unlocalized X_A = X_B + dX_B M of enkf_ism_analysis:
+ * call enkf_ism_analysis for Z (dXB = NULL), then this.
+ *   dXB  nstate x nens deviations (ld ldx); V nobs x nens (ld ldv); Z nobs x nens (ld ldz);
+ *   XB   nstate x nens (ld ldb); XA nstate x nens output (ld lda).  XA may be XB itself
+ *        (same pointer and ld); any other overlap of XA with an input is ENKF_ERR_ARG.
+ * precision ENKF_FP64 or ENKF_FP32; 2 <= nens <= 256; length > 0 (+inf gives delta = 1
+ * inside the radius); radius < 0 means no cut-off.  Every pair (i, j) within the radius
+ * costs 4 Nens flops (FP32 or FP64 CUDA cores); with a radius only the band of each
+ * 32-row tile is visited.  Allocates nothing.
+ */
+ENKF_API enkf_status enkf_localized_update(int64_t nstate, int64_t nobs, int32_t nens, int32_t precision,
+                                           int32_t obs_stride, double length, double radius, const void* dXB,
+                                           int64_t ldx, const void* V, int64_t ldv, const void* Z, int64_t ldz,
+                                           const void* XB, int64_t ldb, void* XA, int64_t lda, void* stream);
+
+/*
+ * Block-diagonal R = diag(R_1, ..., R_nblk) (Sec. 3.1: R^{-1} applied block by block in
+ * Step 1).  Block b covers observation rows [b bs, min(nobs, (b + 1) bs)) and is stored
+ * dense, column-major, FP64, in the leading part of the bs x bs matrix at
+ * Rblk + b bs bs (nblk = ceil(nobs / bs) blocks, 1 <= bs <= 32).  With R = L L^T the
+ * system (R + V V^T) Z = D is (I + V~ V~^T) Z~ = D~ with V~ = L^{-1} V, D~ = L^{-1} D and
+ * Z = L^{-T} Z~; V^T Z = V~^T Z~, so the analysis of the whitened data with r = 1 gives
+ * the same gamma_k, M and X_A.  Sequence: enkf_rblock_factor once per R, then per analysis
+ * enkf_rblock_whiten (V and D in place), enkf_ism_analysis with r = 1, and
+ * enkf_rblock_unwhiten on Z when Z itself is wanted.
+ *   enkf_rblock_factor:   Lblk <- lower Cholesky factors (same layout as Rblk, upper parts
+ *                         zero).  A block that is not positive definite gets NaN factors,
+ *                         which the analysis then reports as ENKF_ERR_NUMERIC.
+ *   enkf_rblock_whiten:   V <- L^{-1} V and, when D != NULL, D <- L^{-1} D (nobs x nens).
+ *   enkf_rblock_unwhiten: Z <- L^{-T} Z (nobs x ncols).
+ * precision ENKF_FP64 or ENKF_FP32 (element type of V, D, Z; the factors are FP64 and the
+ * substitutions run in FP64).  All pointers are device pointers.  Allocates nothing.
+ */
+ENKF_API enkf_status enkf_rblock_factor(int64_t nobs, int32_t bs, const double* Rblk, double* Lblk, void* stream);
+ENKF_API enkf_status enkf_rblock_whiten(int64_t nobs, int32_t nens, int32_t precision, int32_t bs,
+                                        const double* Lblk, void* V, int64_t ldv, void* D, int64_t ldd,
+                                        void* stream);
+ENKF_API enkf_status enkf_rblock_unwhiten(int64_t nobs, int32_t ncols, int32_t precision, int32_t bs,
+                                          const double* Lblk, void* Z, int64_t ldz, void* stream);
+
+/*
  * Kernel-phase timing (tracing aid).  enkf_ism_profile(plan, 1) makes every later
  * enkf_obs_prep / enkf_ism_analysis call on the plan record CUDA events around
  * each of its kernel phases on the caller's stream (up to 4096 phases between

@@ -5,7 +5,9 @@ Each cycle: forecast every member (RK4 ``substeps`` steps, or one application
 of the learned surrogate, or persistence), propagate the truth with RK4, draw
 the observations y = H truth + noise and perturbations (host draws from
 ``synth``), then the analysis: enkf_obs_prep (deviations, V, D) and
-enkf_ism_analysis, X_A written over X_B.  The RMSE is the time mean of the
+enkf_ism_analysis, X_A written over X_B.  Optionally the prep inflates the
+ensemble first (enkf_inflate_prep, Sec. 3.1.1) and the update is localized
+(Z from enkf_ism_analysis, then enkf_localized_update, Sec. 3.1.2).  The RMSE is the time mean of the
 per-cycle root mean square error of the ensemble mean (Sec. 4.1).
 
 This module is orchestration only: the forecast, the prep and the analysis run
@@ -25,7 +27,8 @@ from . import enkf
 
 class LorenzCycle:
     def __init__(self, nstate=4096, nens=256, obs_stride=2, r=0.25, forcing=8.0, dt=0.01, substeps=5,
-                 mode=enkf.ENKF_FP32, seed=None, device="cuda", spinup=1000):
+                 mode=enkf.ENKF_FP32, seed=None, device="cuda", spinup=1000, inflation=1.0, loc_length=None,
+                 loc_radius=None):
         import torch
         self.torch = torch
         self.nstate, self.nens, self.stride, self.r, self.F, self.dt = nstate, nens, obs_stride, r, forcing, dt
@@ -44,6 +47,8 @@ class LorenzCycle:
         self.Y = torch.empty(nens, self.nobs, device=self.dev)
         self.rvec = torch.full((self.nobs,), r, device=self.dev)
         self.plan = enkf.Plan(nstate, self.nobs, nens, mode, device=self.dev)
+        self.inflation, self.loc_length, self.loc_radius = float(inflation), loc_length, loc_radius
+        self.Z = torch.empty(nens, self.nobs, device=self.dev, dtype=self.X.dtype) if loc_length else None
         self.cycle_index = 0
         self.sur_packed = None
         self.sur_ws = None
@@ -68,8 +73,16 @@ class LorenzCycle:
         draws = synth.lorenz_cycle_draws(self.cycle_index, self.nstate, self.nens, self.stride, self.r, self.seed)
         y = self.truth[0, ::self.stride].float() + torch.from_numpy(draws["obs_noise"]).to(self.dev).float()
         self.Y.copy_(y[None, :] + torch.from_numpy(draws["pert"]).to(self.dev).float())
-        self.plan.obs_prep(self.stride, 1, self.X, self.dX, self.V, Y=self.Y, D=self.D)
-        self.plan.analysis(self.rvec, self.V, self.D, dXB=self.dX, XB=self.X, XA=self.X)
+        if self.inflation != 1.0:
+            enkf.enkf_inflate_prep(self.stride, self.inflation, self.X, self.V, dXB=self.dX, Y=self.Y, D=self.D)
+        else:
+            self.plan.obs_prep(self.stride, 1, self.X, self.dX, self.V, Y=self.Y, D=self.D)
+        if self.Z is not None:
+            self.plan.analysis(self.rvec, self.V, self.D, Z=self.Z)
+            enkf.enkf_localized_update(self.stride, self.loc_length, self.loc_radius, self.dX, self.V, self.Z,
+                                       self.X, self.X)
+        else:
+            self.plan.analysis(self.rvec, self.V, self.D, dXB=self.dX, XB=self.X, XA=self.X)
         self.cycle_index += 1
 
     def rmse(self):

@@ -104,6 +104,18 @@ def load(build_if_missing: bool = False):
         lib.enkf_ism_solve_noalloc.argtypes = [i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp,
                                                ctypes.POINTER(i32)]
         lib.enkf_ism_solve_noalloc.restype = ctypes.c_int
+        lib.enkf_inflate_prep.argtypes = [i64, i64, i32, i32, i32, dbl, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64,
+                                          vp]
+        lib.enkf_inflate_prep.restype = ctypes.c_int
+        lib.enkf_localized_update.argtypes = [i64, i64, i32, i32, i32, dbl, dbl, vp, i64, vp, i64, vp, i64, vp, i64,
+                                              vp, i64, vp]
+        lib.enkf_localized_update.restype = ctypes.c_int
+        lib.enkf_rblock_factor.argtypes = [i64, i32, vp, vp, vp]
+        lib.enkf_rblock_factor.restype = ctypes.c_int
+        lib.enkf_rblock_whiten.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp, i64, vp]
+        lib.enkf_rblock_whiten.restype = ctypes.c_int
+        lib.enkf_rblock_unwhiten.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp]
+        lib.enkf_rblock_unwhiten.restype = ctypes.c_int
         lib.enkf_ism_batch_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(enkf_ism_problem), i32, u32,
                                             ctypes.POINTER(sz)]
         lib.enkf_ism_batch_plan.restype = ctypes.c_int
@@ -243,6 +255,61 @@ def enkf_ism_solve_noalloc(r, V, D, Z, stream=None, sync: bool = True) -> int:
     _check(load().enkf_ism_solve_noalloc(nobs, nens, precision, _ptr(r, "r"), pV, ldv, pD, ldd, pZ, ldz,
                                          _stream(stream), ctypes.byref(st) if sync else None))
     return st.value
+
+
+def _precision(t):
+    import torch
+    return ENKF_FP64 if t.dtype == torch.float64 else ENKF_FP32
+
+
+def enkf_inflate_prep(obs_stride: int, alpha: float, XB, V, dXB=None, Y=None, D=None, stream=None) -> None:
+    """Inflation x <- xbar + alpha (x - xbar) of XB in place, fused with the centering prep
+    (dXB, V, and D when Y is given).  Sizes come from the tensors: XB (nens, nstate), V (nens, nobs)."""
+    pXB, ldb = _mat(XB, "XB")
+    pdX, ldx = _mat(dXB, "dXB")
+    pY, ldy = _mat(Y, "Y")
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    nens, nstate = XB.shape
+    nobs = V.shape[1]
+    _check(load().enkf_inflate_prep(nstate, nobs, nens, _precision(XB), obs_stride, float(alpha), pXB, ldb, pdX,
+                                    ldx, pY, ldy, pV, ldv, pD, ldd, _stream(stream)))
+
+
+def enkf_localized_update(obs_stride: int, length: float, radius, dXB, V, Z, XB, XA, stream=None) -> None:
+    """X_A = X_B + (Delta o (S V^T)) Z (partial localization); radius None = no cut-off.
+    dXB, XB, XA: (nens, nstate); V, Z: (nens, nobs).  XA may be XB."""
+    pdX, ldx = _mat(dXB, "dXB")
+    pV, ldv = _mat(V, "V")
+    pZ, ldz = _mat(Z, "Z")
+    pXB, ldb = _mat(XB, "XB")
+    pXA, lda = _mat(XA, "XA")
+    nens, nstate = dXB.shape
+    nobs = V.shape[1]
+    rad = -1.0 if radius is None else float(radius)
+    _check(load().enkf_localized_update(nstate, nobs, nens, _precision(dXB), obs_stride, float(length), rad, pdX, ldx,
+                                        pV, ldv, pZ, ldz, pXB, ldb, pXA, lda, _stream(stream)))
+
+
+def enkf_rblock_factor(nobs: int, bs: int, Rblk, Lblk, stream=None) -> None:
+    """Lblk <- block Cholesky factors of Rblk (CUDA float64 tensors of nblk * bs * bs entries)."""
+    _check(load().enkf_rblock_factor(nobs, bs, _ptr(Rblk, "Rblk"), _ptr(Lblk, "Lblk"), _stream(stream)))
+
+
+def enkf_rblock_whiten(bs: int, Lblk, V, D=None, stream=None) -> None:
+    """V <- L^{-1} V, D <- L^{-1} D in place (V, D: (nens, nobs))."""
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    nens, nobs = V.shape
+    _check(load().enkf_rblock_whiten(nobs, nens, _precision(V), bs, _ptr(Lblk, "Lblk"), pV, ldv, pD, ldd,
+                                     _stream(stream)))
+
+
+def enkf_rblock_unwhiten(bs: int, Lblk, Z, stream=None) -> None:
+    """Z <- L^{-T} Z in place (Z: (ncols, nobs))."""
+    pZ, ldz = _mat(Z, "Z")
+    ncols, nobs = Z.shape
+    _check(load().enkf_rblock_unwhiten(nobs, ncols, _precision(Z), bs, _ptr(Lblk, "Lblk"), pZ, ldz, _stream(stream)))
 
 
 def enkf_ism_batch_plan(problems, mode: int = ENKF_FP32, flags: int = 0):

@@ -34,7 +34,7 @@ import threading
 import numpy as np
 
 SEED_BASE = 13023876
-WORKLOADS = ("lorenz_small", "large_single", "panel_single", "batch_local", "lorenz_cycle")
+WORKLOADS = ("lorenz_small", "large_single", "panel_single", "batch_local", "lorenz_cycle", "next_rows")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_DIR = os.path.join(_HERE, "_lib")
