@@ -3,9 +3,10 @@
 // enkf_localized_update (declared in include/enkf_ism.h).
 //
 // enkf_inflate_prep: multiplicative inflation x_i <- xbar + alpha (x_i - xbar)
-// fused into the centering observation prep: one thread per state row reads the
-// row's members once for the mean (FP64) and once more to write the inflated
-// ensemble, its deviations, V = H dX_B / sqrt(Nens - 1) and D = Y - H X_B.
+// fused into the centering observation prep: the row's members are read once for the
+// mean and once more to write the inflated ensemble, its deviations,
+// V = H dX_B / sqrt(Nens - 1) and D = Y - H X_B (FP64 storage: one thread per row, FP64
+// arithmetic; FP32 storage: 32-row tiles, compensated FP32 arithmetic).
 //
 // enkf_localized_update: X_A = X_B + (Delta o (S V^T)) Z, S = dX_B / sqrt(Nens - 1),
 // Delta = (delta_ij) the impact factors of observation j on state component i:
@@ -68,6 +69,74 @@ __global__ void inflate_center_observe_kernel(int64_t nstate, int64_t nobs, int 
                 if (Y) D[(int64_t)e * ldd + j] = Y[(int64_t)e * ldy + j] - xi;
             }
         }
+    }
+}
+
+// FP32 storage: FP32 arithmetic only (per-element FP64 arithmetic and conversions would run on
+// GB300's narrow FP64 pipe).  A CTA takes tiles of 32 rows; lane = row, warp w sums members
+// w, w + 8, ... with a compensated (Neumaier) FP32 sum, the eight partials are combined in a
+// fixed order, and the mean is kept as an unevaluated pair mh + ml (ml = the rounding residual
+// of mh), so deviations are formed as (x - mh) - ml.  The second pass re-reads the tile (16 KB at
+// 128 members, an L2 hit) and writes the outputs.  alpha == 1 leaves X_B untouched.
+constexpr int kInfWarps = 8;
+
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(kInfWarps * 32) inflate_prep_f32_kernel(
+    int64_t nstate, int64_t nobs, int n, int stride, float alpha, int inflate, float* __restrict__ XB, int64_t ldb,
+    float* __restrict__ dXB, int64_t ldx, const float* __restrict__ Y, int64_t ldy, float* __restrict__ V,
+    int64_t ldv, float* __restrict__ D, int64_t ldd, float scale) {
+    __shared__ float ps[kInfWarps][32], pc[kInfWarps][32], mhs[32], mls[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i0 = (int64_t)blockIdx.x * 32; i0 < nstate; i0 += (int64_t)gridDim.x * 32) {
+        const int64_t i = i0 + lane;
+        const bool in = i < nstate;
+        float s = 0.f, c = 0.f;
+        if (in) {
+#pragma unroll 4
+            for (int e = warp; e < n; e += kInfWarps) neumaier_add(s, c, XB[(int64_t)e * ldb + i]);
+        }
+        ps[warp][lane] = s;
+        pc[warp][lane] = c;
+        __syncthreads();
+        if (warp == 0) {
+            float S = 0.f, C = 0.f;
+            for (int w = 0; w < kInfWarps; ++w) {
+                neumaier_add(S, C, ps[w][lane]);
+                C += pc[w][lane];
+            }
+            const float tot = S + C;
+            const float lo = C - (tot - S);                       // S + C = tot + lo
+            const float mh = tot / (float)n;
+            const float ml = (fmaf(-mh, (float)n, tot) + lo) / (float)n;
+            mhs[lane] = mh;
+            mls[lane] = ml;
+        }
+        __syncthreads();
+        const float mh = mhs[lane], ml = mls[lane];
+        const bool observed = in && (i % stride == 0) && (i / stride < nobs);
+        const int64_t j = i / stride;
+        if (in) {
+            for (int e = warp; e < n; e += kInfWarps) {
+                const float x = XB[(int64_t)e * ldb + i];
+                float xi = x;
+                if (inflate) {
+                    xi = mh + fmaf(alpha, (x - mh) - ml, ml);
+                    XB[(int64_t)e * ldb + i] = xi;
+                }
+                const float d = (xi - mh) - ml;
+                if (dXB) dXB[(int64_t)e * ldx + i] = d;
+                if (observed) {
+                    V[(int64_t)e * ldv + j] = d * scale;
+                    if (Y) D[(int64_t)e * ldd + j] = Y[(int64_t)e * ldy + j] - xi;
+                }
+            }
+        }
+        __syncthreads();                                         // ps / mhs reused by the next tile
     }
 }
 
@@ -279,16 +348,19 @@ extern "C" enkf_status enkf_inflate_prep(int64_t nstate, int64_t nobs, int32_t n
     if (ldb < nstate || (dXB && ldx < nstate) || ldv < nobs || (Y && (ldy < nobs || ldd < nobs)))
         return lfail(ENKF_ERR_SHAPE, "enkf_inflate_prep: leading dimension smaller than the rows");
     const double scale = 1.0 / sqrt((double)(nens - 1));
-    const int blocks = (int)((nstate + 255) / 256);
     cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)((nstate + 255) / 256);
     if (precision == ENKF_FP64)
         inflate_center_observe_kernel<double><<<blocks, 256, 0, s>>>(
             nstate, nobs, nens, obs_stride, alpha, (double*)XB, ldb, (double*)dXB, ldx, (const double*)Y, ldy,
             (double*)V, ldv, (double*)D, ldd, scale);
-    else
-        inflate_center_observe_kernel<float><<<blocks, 256, 0, s>>>(
-            nstate, nobs, nens, obs_stride, alpha, (float*)XB, ldb, (float*)dXB, ldx, (const float*)Y, ldy,
-            (float*)V, ldv, (float*)D, ldd, scale);
+    else {
+        int64_t tiles = (nstate + 31) / 32;
+        if (tiles > 152 * 64) tiles = 152 * 64;
+        inflate_prep_f32_kernel<<<(unsigned)tiles, kInfWarps * 32, 0, s>>>(
+            nstate, nobs, nens, obs_stride, (float)alpha, alpha != 1.0, (float*)XB, ldb, (float*)dXB, ldx,
+            (const float*)Y, ldy, (float*)V, ldv, (float*)D, ldd, (float)scale);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return lcuda(e, "enkf_inflate_prep: launch");
     return ENKF_OK;

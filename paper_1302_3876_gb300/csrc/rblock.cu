@@ -11,9 +11,10 @@
 // of the unchanged analysis run on (r = 1, V~, D~).
 //
 // enkf_rblock_factor: one warp per block, right-looking Cholesky in shared memory
-// (FP64), lane q owning row q.  enkf_rblock_whiten / enkf_rblock_unwhiten: one warp
-// per (block, column), forward (L y = b) or backward (L^T x = y) substitution with
-// the solved entry broadcast by a shuffle; FP64 arithmetic for both storage types.
+// (FP64), lane q owning row q.  enkf_rblock_whiten / enkf_rblock_unwhiten: one lane per
+// column of a block, forward (L y = b) or backward (L^T x = y) substitution in
+// registers with the factor and its reciprocal diagonal broadcast from shared memory,
+// in the storage precision (FP32 or FP64).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -79,54 +80,95 @@ __global__ void __launch_bounds__(kFactorWarps * 32) rblock_factor_kernel(int64_
         if (lane < bs) Lb[(int64_t)c * bs + lane] = !ok ? nan : (lane >= c && lane < m && c < m) ? A[lane * kRbPitch + c] : 0.0;
 }
 
-// blockIdx.x = block of R, blockIdx.y * kSolveWarps + warp = column (first ncol0 of A0, then A1).
+// blockIdx.x = block of R; warp w of CTA blockIdx.y owns columns (blockIdx.y * kSolveWarps + w) * 32 + lane
+// (first ncol0 of A0, then A1), one column per lane.  A warp stages its 32 columns of the block
+// through shared memory (column loads are contiguous runs of the block's rows), substitutes in
+// registers with L and the reciprocal diagonal broadcast from shared memory, and stores back the
+// same way.  Arithmetic in the storage type (FP32 or FP64); the factors are FP64 in memory.
+template <typename T>
+constexpr int solve_warps() { return sizeof(T) == 8 ? kSolveWarps / 2 : kSolveWarps; }   // static smem <= 48 KB
+
 template <typename T, bool kForward>
-__global__ void __launch_bounds__(kSolveWarps * 32) rblock_solve_kernel(int64_t nobs, int bs,
+__global__ void __launch_bounds__(solve_warps<T>() * 32) rblock_solve_kernel(int64_t nobs, int bs,
                                                                         const double* __restrict__ L, T* A0,
                                                                         int64_t ld0, int ncol0, T* A1, int64_t ld1,
                                                                         int ncol1) {
-    __shared__ double Ls[kRbMax * kRbPitch];               // Ls[row * pitch + col]
+    __shared__ T Ls[kRbMax * kRbPitch];                    // Ls[row * pitch + col], zero outside m x m
+    __shared__ T inv[kRbMax];
+    constexpr int W = solve_warps<T>();
+    __shared__ T tile[W][32 * kRbPitch];                   // tile[column * pitch + row]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t b = blockIdx.x;
     const int64_t r0 = b * bs;
     const int m = (int)((nobs - r0) < bs ? (nobs - r0) : bs);
     const double* Lb = L + b * (int64_t)bs * bs;
-    for (int idx = threadIdx.x; idx < kRbMax * kRbMax; idx += kSolveWarps * 32) {
+    for (int idx = threadIdx.x; idx < kRbMax * kRbMax; idx += W * 32) {
         const int row = idx % kRbMax, col = idx / kRbMax;
-        Ls[row * kRbPitch + col] = (row < m && col < m) ? Lb[(int64_t)col * bs + row] : 0.0;
+        Ls[row * kRbPitch + col] = (row < m && col < m) ? (T)Lb[(int64_t)col * bs + row] : T(0);
     }
+    if (threadIdx.x < kRbMax) inv[threadIdx.x] = threadIdx.x < m ? (T)(1.0 / Lb[(int64_t)threadIdx.x * bs + threadIdx.x]) : T(0);
     __syncthreads();
-    const int col = blockIdx.y * kSolveWarps + warp;
-    if (col >= ncol0 + ncol1) return;
-    T* x = col < ncol0 ? A0 + (int64_t)col * ld0 + r0 : A1 + (int64_t)(col - ncol0) * ld1 + r0;
-    double val = lane < m ? (double)x[lane] : 0.0;
+    const int ncol = ncol0 + ncol1;
+    const int cbase = (blockIdx.y * W + warp) * 32;
+    if (cbase >= ncol) return;
+    T* tw = tile[warp];
+    // stage: column cc of the warp, rows r0 .. r0 + m - 1 (lane = row)
+    for (int cc = 0; cc < 32; ++cc) {
+        const int col = cbase + cc;
+        T v = T(0);
+        if (col < ncol && lane < m) {
+            const T* x = col < ncol0 ? A0 + (int64_t)col * ld0 : A1 + (int64_t)(col - ncol0) * ld1;
+            v = x[r0 + lane];
+        }
+        tw[cc * kRbPitch + lane] = v;
+    }
+    __syncwarp();
+    T y[kRbMax];
     if (kForward) {
-        for (int c = 0; c < m; ++c) {
-            const double xc = __shfl_sync(0xffffffffu, val, c) / Ls[c * kRbPitch + c];
-            if (lane == c) val = xc;
-            else if (lane > c) val -= Ls[lane * kRbPitch + c] * xc;
+#pragma unroll
+        for (int c = 0; c < kRbMax; ++c) {
+            T acc = tw[lane * kRbPitch + c];
+#pragma unroll
+            for (int p = 0; p < c; ++p) acc -= Ls[c * kRbPitch + p] * y[p];
+            y[c] = acc * inv[c];                           // rows >= m: L and inv are zero, y = 0
         }
     } else {
-        for (int c = m - 1; c >= 0; --c) {
-            const double xc = __shfl_sync(0xffffffffu, val, c) / Ls[c * kRbPitch + c];
-            if (lane == c) val = xc;
-            else if (lane < c) val -= Ls[c * kRbPitch + lane] * xc;
+#pragma unroll
+        for (int c = kRbMax - 1; c >= 0; --c) {
+            T acc = tw[lane * kRbPitch + c];
+#pragma unroll
+            for (int p = c + 1; p < kRbMax; ++p) acc -= Ls[p * kRbPitch + c] * y[p];
+            y[c] = acc * inv[c];
         }
     }
-    if (lane < m) x[lane] = (T)val;
+#pragma unroll
+    for (int c = 0; c < kRbMax; ++c) tw[lane * kRbPitch + c] = y[c];
+    __syncwarp();
+    for (int cc = 0; cc < 32; ++cc) {
+        const int col = cbase + cc;
+        if (col < ncol && lane < m) {
+            T* x = col < ncol0 ? A0 + (int64_t)col * ld0 : A1 + (int64_t)(col - ncol0) * ld1;
+            x[r0 + lane] = tw[cc * kRbPitch + lane];
+        }
+    }
 }
 
 template <bool kForward>
 cudaError_t rblock_solve(bool fp64, int64_t nobs, int bs, const double* L, void* A0, int64_t ld0, int ncol0, void* A1,
                          int64_t ld1, int ncol1, cudaStream_t s) {
     const int64_t nblk = (nobs + bs - 1) / bs;
-    dim3 grid((unsigned)nblk, (unsigned)((ncol0 + ncol1 + kSolveWarps - 1) / kSolveWarps));
-    if (fp64)
-        rblock_solve_kernel<double, kForward><<<grid, kSolveWarps * 32, 0, s>>>(nobs, bs, L, (double*)A0, ld0, ncol0,
-                                                                               (double*)A1, ld1, ncol1);
-    else
-        rblock_solve_kernel<float, kForward><<<grid, kSolveWarps * 32, 0, s>>>(nobs, bs, L, (float*)A0, ld0, ncol0,
-                                                                              (float*)A1, ld1, ncol1);
+    const int cols = ncol0 + ncol1;
+    if (fp64) {
+        constexpr int W = solve_warps<double>();
+        dim3 grid((unsigned)nblk, (unsigned)((cols + 32 * W - 1) / (32 * W)));
+        rblock_solve_kernel<double, kForward><<<grid, W * 32, 0, s>>>(nobs, bs, L, (double*)A0, ld0, ncol0,
+                                                                     (double*)A1, ld1, ncol1);
+    } else {
+        constexpr int W = solve_warps<float>();
+        dim3 grid((unsigned)nblk, (unsigned)((cols + 32 * W - 1) / (32 * W)));
+        rblock_solve_kernel<float, kForward><<<grid, W * 32, 0, s>>>(nobs, bs, L, (float*)A0, ld0, ncol0,
+                                                                    (float*)A1, ld1, ncol1);
+    }
     return cudaGetLastError();
 }
 
@@ -165,7 +207,7 @@ extern "C" enkf_status enkf_rblock_whiten(int64_t nobs, int32_t nens, int32_t pr
         return rfail(ENKF_ERR_ARG, "enkf_rblock_whiten: precision must be ENKF_FP64 or ENKF_FP32");
     enkf_status st = check_sizes("enkf_rblock_whiten", nobs, bs);
     if (st != ENKF_OK) return st;
-    if (nens < 1 || nens > 65535 * kSolveWarps / 2) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_whiten: bad nens");
+    if (nens < 1 || nens > 65535 * 16) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_whiten: bad nens");
     if (ldv < nobs || (D && ldd < nobs)) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_whiten: ld smaller than nobs");
     const uintptr_t wmask = precision == ENKF_FP64 ? 7 : 3;
     if ((((uintptr_t)V | (uintptr_t)D) & wmask) || ((uintptr_t)Lblk & 7))
@@ -183,7 +225,7 @@ extern "C" enkf_status enkf_rblock_unwhiten(int64_t nobs, int32_t ncols, int32_t
         return rfail(ENKF_ERR_ARG, "enkf_rblock_unwhiten: precision must be ENKF_FP64 or ENKF_FP32");
     enkf_status st = check_sizes("enkf_rblock_unwhiten", nobs, bs);
     if (st != ENKF_OK) return st;
-    if (ncols < 1 || ncols > 65535 * kSolveWarps) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_unwhiten: bad ncols");
+    if (ncols < 1 || ncols > 65535 * 32) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_unwhiten: bad ncols");
     if (ldz < nobs) return rfail(ENKF_ERR_SHAPE, "enkf_rblock_unwhiten: ldz smaller than nobs");
     if (((uintptr_t)Z & (precision == ENKF_FP64 ? 7 : 3)) || ((uintptr_t)Lblk & 7))
         return rfail(ENKF_ERR_ARG, "enkf_rblock_unwhiten: pointer not aligned to the element size");
