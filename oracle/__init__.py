@@ -61,6 +61,7 @@ def _load():
                 "oracle_l96_rhs": ([i64, vp, dbl, vp], None),
                 "oracle_l96_rk4": ([i64, i32, vp, i64, dbl, dbl, i32], ctypes.c_int),
                 "oracle_inflate": ([i64, i32, dbl, vp, i64], None),
+                "oracle_ism_step2_pivot": ([i64, i32, i32, vp, i64, vp, i64, vp, i64, vp, vp, vp], ctypes.c_int),
                 "oracle_localized_increment_literal": ([i64, i64, i32, i32, i32, dbl, dbl, vp, i64, vp, i64, vp,
                                                         i64, vp, i64], None),
                 "oracle_localized_update": ([i64, i64, i32, i32, i32, dbl, dbl, vp, i64, vp, i64, vp, i64, vp,
@@ -185,6 +186,25 @@ def ism_levels(V, U, Z, nobs=None):
     if st != 0:
         raise FloatingPointError(f"iterative Sherman-Morrison stopped at level {st}")
     return gamma[:V.shape[0]]
+
+
+def ism_solve_pivot(r, V, D, count_longops=False):
+    """Z = S_*(R, V, D) with the pivoting of Sec. 3.4: Step 1, then Step 2 choosing at each level
+    the remaining column with the largest |gamma|.  Returns (Z, gamma in level order, perm[, longops]),
+    perm[k] = the original column index used at level k."""
+    U, Z = ism_step1(r, V, D)
+    V = _f64(np.ascontiguousarray(V[:, :r.shape[0]]), "V")
+    nobs = r.shape[0]
+    nens, nrhs = V.shape[0], Z.shape[0]
+    gamma = np.zeros(max(nens, 1))
+    perm = np.zeros(max(nens, 1), dtype=np.int32)
+    ops = ctypes.c_int64(nobs * (nens + nrhs))            # Step 1: one division per entry of U and Z
+    st = _load().oracle_ism_step2_pivot(nobs, nens, nrhs, _p(V), nobs, _p(U), nobs, _p(Z), nobs, _p(gamma),
+                                        ctypes.c_void_p(perm.ctypes.data), ctypes.byref(ops))
+    if st != 0:
+        raise FloatingPointError(f"iterative Sherman-Morrison stopped at level {st}")
+    out = (Z, gamma[:nens], perm[:nens])
+    return out + (int(ops.value),) if count_longops else out
 
 
 def vtz(V, Z, nobs=None):

@@ -423,3 +423,76 @@ int oracle_ism_step1_blockdiag(int64_t nobs, int32_t nens, int32_t nrhs, int32_t
     }
     return status;
 }
+
+/*
+ * Step 2 with pivoting (Sec. 3.4, eq. EnKSM:gamma-value): before level k the
+ * candidate with the largest |1 + v_i^T u_i^(k-1)| over k <= i < Nens (0-based;
+ * ties go to the lowest index) is found, and columns k and that index are
+ * interchanged in V and U^(k-1) (the columns of Z are right-hand sides and stay
+ * where they are); then level k runs as in oracle_ism_step2.  V is copied first
+ * (the caller's V is not modified).  perm[k] receives the original column index
+ * that level k used; gamma[k] its gamma_k.  Long operations as in
+ * oracle_ism_step2 plus Nobs products per candidate (Sec. 3.4 counts every
+ * candidate, the pivot included, on top of T_SMF).
+ */
+int oracle_ism_step2_pivot(int64_t nobs, int32_t nens, int32_t nrhs, const double* V, int64_t ldv, double* U,
+                           int64_t ldu, double* Z, int64_t ldz, double* gamma, int32_t* perm, int64_t* longops) {
+    double* Vc = (double*)malloc(sizeof(double) * (size_t)(nobs > 0 ? nobs : 1) * (size_t)(nens > 0 ? nens : 1));
+    double* h = (double*)malloc(sizeof(double) * (size_t)(nobs > 0 ? nobs : 1));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(nens > 0 ? nens : 1));
+    if (!Vc || !h || !g) {
+        free(Vc);
+        free(h);
+        free(g);
+        return -1;
+    }
+    for (int32_t i = 0; i < nens; ++i) {
+        memcpy(Vc + i * nobs, V + i * ldv, sizeof(double) * (size_t)nobs);
+        perm[i] = i;
+    }
+    int status = 0;
+    for (int32_t k = 0; k < nens; ++k) {
+#pragma omp parallel for schedule(static)
+        for (int32_t i = k; i < nens; ++i) g[i] = 1.0 + dot_asc(nobs, Vc + i * nobs, U + i * ldu);
+        if (longops) *longops += (int64_t)(nens - k) * nobs;
+        int32_t ind = k;
+        for (int32_t i = k + 1; i < nens; ++i)
+            if (fabs(g[i]) > fabs(g[ind])) ind = i;
+        if (ind != k) {
+            for (int64_t j = 0; j < nobs; ++j) {
+                double t = Vc[k * nobs + j];
+                Vc[k * nobs + j] = Vc[ind * nobs + j];
+                Vc[ind * nobs + j] = t;
+                t = U[k * ldu + j];
+                U[k * ldu + j] = U[ind * ldu + j];
+                U[ind * ldu + j] = t;
+            }
+            int32_t t = perm[k];
+            perm[k] = perm[ind];
+            perm[ind] = t;
+        }
+        const double* vk = Vc + k * nobs;
+        const double* uk = U + k * ldu;
+        double gk = g[ind];
+        if (gamma) gamma[k] = gk;
+        if (!(gk > 0.0) || !isfinite(gk)) { status = k + 1; break; }
+        for (int64_t j = 0; j < nobs; ++j) h[j] = uk[j] / gk;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t i = 0; i < nrhs; ++i) {
+            double* z = Z + i * ldz;
+            double c = dot_asc(nobs, vk, z);
+            for (int64_t j = 0; j < nobs; ++j) z[j] -= h[j] * c;
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t i = k + 1; i < nens; ++i) {
+            double* u = U + i * ldu;
+            double c = dot_asc(nobs, vk, u);
+            for (int64_t j = 0; j < nobs; ++j) u[j] -= h[j] * c;
+        }
+        if (longops) *longops += 2 * nobs + 2 * nobs * (int64_t)nrhs + 2 * nobs * (int64_t)(nens - 1 - k);
+    }
+    free(Vc);
+    free(h);
+    free(g);
+    return status;
+}

@@ -198,3 +198,52 @@ def test_block_not_positive_definite_is_rejected():
     D = synth.normal_matrix(98, 2, 12, 3)
     with pytest.raises(FloatingPointError, match="block 1"):
         oracle.ism_step1_blockdiag(Rblk, V, D)
+
+
+# ----------------------------------------------------------------------------------------------
+# pivoting (Sec. 3.4)
+# ----------------------------------------------------------------------------------------------
+
+def _piv_problem(seed, nobs, nens):
+    r = synth.uniform(seed, 1, nobs, 0.5, 1.5)
+    V = synth.normal_matrix(seed, 2, nobs, nens, std=1.0 / math.sqrt(nens - 1),
+                            row_scale=synth.uniform(seed, 5, nobs, 0.2, 3.0))
+    D = synth.normal_matrix(seed, 3, nobs, nens)
+    return r, V, D
+
+
+@pytest.mark.parametrize("nobs,nens", [(30, 4), (64, 9), (200, 16), (17, 17)])
+def test_pivoted_solve_equals_dense_cholesky_and_the_unpivoted_solve(nobs, nens):
+    r, V, D = _piv_problem(401 + nobs, nobs, nens)
+    Z, gamma, perm = oracle.ism_solve_pivot(r, V, D)
+    W = np.diag(r) + V.T @ V
+    want = sla.cho_solve(sla.cho_factor(W), D.T).T
+    np.testing.assert_allclose(Z, want, rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(Z, oracle.ism_solve(r, V, D), rtol=1e-11, atol=1e-12)
+    assert sorted(perm.tolist()) == list(range(nens))
+    assert np.all(gamma >= 1.0)
+
+
+@pytest.mark.parametrize("nobs,nens", [(12, 3), (20, 5), (9, 6)])
+def test_pivot_is_the_largest_gamma_among_the_remaining_columns(nobs, nens):
+    """Brute force of eq. EnKSM:gamma-value: at level k the candidate gamma of column i is
+    1 + v_i^T W^{-1} v_i with W = R + sum of v v^T over the columns already used (dense solve)."""
+    r, V, D = _piv_problem(433 + nobs, nobs, nens)
+    _, gamma, perm = oracle.ism_solve_pivot(r, V, D)
+    used = []
+    for k in range(nens):
+        W = np.diag(r) + sum((np.outer(V[p], V[p]) for p in used), np.zeros((nobs, nobs)))
+        cand = {i: 1.0 + V[i] @ np.linalg.solve(W, V[i]) for i in range(nens) if i not in used}
+        best = max(cand, key=lambda i: (abs(cand[i]), -i))
+        assert perm[k] == best
+        assert gamma[k] == pytest.approx(cand[best], rel=1e-12)
+        used.append(best)
+    assert perm.tolist() != list(range(nens))    # these inputs do reorder the columns
+
+
+@pytest.mark.parametrize("nobs,nens", [(40, 7), (100, 12)])
+def test_pivoted_long_operation_count_is_seven_halves(nobs, nens):
+    """Sec. 3.4: T_SMF^PIV = 3 (N^2 Nobs + N Nobs) + Nobs per candidate = (7/2)(N^2 Nobs + N Nobs)."""
+    r, V, D = _piv_problem(461, nobs, nens)
+    _, _, _, ops = oracle.ism_solve_pivot(r, V, D, count_longops=True)
+    assert ops == 7 * (nens * nens * nobs + nens * nobs) // 2
