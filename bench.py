@@ -748,6 +748,37 @@ def run_next_rows(args):
                                 "fp64_gflop": nobs * 2 * nens * bs / 1e9}}
         del A, R, L, dX, D0, V, D, Z, XA
 
+    if part in ("all", "pivot"):
+        nobs, nens = 1 << 18, 64
+        res = {}
+        for name, dt, mode in (("fp32", torch.float32, enkf.ENKF_FP32), ("fp64", torch.float64, enkf.ENKF_FP64)):
+            r = 0.5 + torch.rand(nobs, device=dev, generator=gen, dtype=dt)
+            V = torch.randn(nens, nobs, device=dev, generator=gen, dtype=dt) / math.sqrt(nens - 1)
+            D = torch.randn(nens, nobs, device=dev, generator=gen, dtype=dt)
+            Z = torch.empty_like(D)
+            M = torch.empty(nens * nens, device=dev, dtype=dt)
+            ws = torch.empty(enkf.enkf_ism_pivot_workspace(nobs, nens, mode), dtype=torch.uint8, device=dev)
+            fn = lambda: enkf.enkf_ism_solve_pivot(r, V, D, Z, ws, M=M, sync=False)  # noqa: E731
+            for _ in range(args.warmup):
+                fn()
+            ms = _events_ms(fn, min(k, 10))
+            plan = enkf.Plan(1, nobs, nens, mode, device=dev)
+            fn0 = lambda: plan.analysis(r, V, D, Z=Z, M=M)  # noqa: E731
+            for _ in range(args.warmup):
+                fn0()
+            ms0 = _events_ms(fn0, min(k, 10))
+            plan.close()
+            w = 4 if dt == torch.float32 else 8
+            # per level: the dots pass reads v_p and the active columns, the update pass reads and
+            # writes them and reads the remaining v_i (their dots for the next choice)
+            nbytes = sum(w * nobs * (1 + (nens + nens - kk) + 2 * (nens + nens - kk - 1) + (nens - kk - 1))
+                         for kk in range(nens))
+            res[name] = {"ms_pivoted": ms, "ms_unpivoted_plain_path": ms0, "launches": 4 * nens + 4,
+                         "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm,
+                                      "unit": "GB/s", "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "bytes": nbytes}}
+            del r, V, D, Z, M, ws
+        out["pivoted_solve"] = {"config": f"Nobs={nobs} Nens={nens}", "paths": res}
+
     if part in ("all", "cycle"):
         # partial localization leaves (R + V V^T)^{-1} unlocalized: with short correlation lengths the
         # cycle diverges (the analysis then reports ENKF_ERR_NUMERIC), which is recorded, not raised
@@ -791,7 +822,7 @@ def main():
     ap.add_argument("--refine", action="store_true", help="one step of iterative refinement (panel modes)")
     ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle",
                                            "next_rows"], default="large_single")
-    ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "cycle"], default="all",
+    ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "pivot", "cycle"], default="all",
                     help="next_rows workload: run one part only")
     ap.add_argument("--cycles", type=int, default=200, help="next_rows workload: assimilation cycles per filter")
     ap.add_argument("--train-cycles", type=int, default=60)

@@ -354,6 +354,30 @@ ENKF_API enkf_status enkf_rblock_unwhiten(int64_t nobs, int32_t ncols, int32_t p
                                           const double* Lblk, void* Z, int64_t ldz, void* stream);
 
 /*
+ * enkf_ism_solve_pivot -- the solve Z = (R + V V^T)^{-1} D with the optional pivoting of
+ * Sec. 3.4 (eq. EnKSM:gamma-value): before level k the remaining column with the largest
+ * |1 + v_i^T u_i^(k-1)| is taken (ties to the lowest index), which the paper offers to
+ * reduce round-off.  Z is the same in exact arithmetic; only the level order changes.
+ *   r, V, D     as for enkf_ism_analysis (R = diag(r)); V and D are not written.
+ *   Z           nobs x nens output (ld ldz), required.
+ *   M           nens x nens output (column-major, ld nens, nullable; nens >= 2):
+ *               V^T Z / sqrt(Nens - 1) in the caller's member order.
+ *   perm        device int32[nens] (nullable): perm[k] = member column used at level k.
+ *   gamma       device double[nens] (nullable): gamma_k of level k.
+ *   workspace   >= enkf_ism_pivot_workspace bytes, 256-byte aligned, caller-owned.
+ *   status      host int or NULL; when given, the call synchronises and stores the
+ *               device status word (r_j <= 0, non-finite values, gamma_k < 1 - tol).
+ * precision ENKF_FP64 or ENKF_FP32 (dots accumulated in FP64); 1 <= nens <= 256.  Four
+ * launches per level (choice, dots, reduction, update) with no grid-wide wait inside a
+ * kernel; the reductions run in a fixed order, so results are reproducible.
+ */
+ENKF_API enkf_status enkf_ism_pivot_workspace(int64_t nobs, int32_t nens, int32_t precision, size_t* bytes);
+ENKF_API enkf_status enkf_ism_solve_pivot(int64_t nobs, int32_t nens, int32_t precision, const void* r,
+                                          const void* V, int64_t ldv, const void* D, int64_t ldd, void* Z,
+                                          int64_t ldz, void* M, int32_t* perm, double* gamma, void* workspace,
+                                          size_t workspace_bytes, void* stream, int32_t* status);
+
+/*
  * Kernel-phase timing (tracing aid).  enkf_ism_profile(plan, 1) makes every later
  * enkf_obs_prep / enkf_ism_analysis call on the plan record CUDA events around
  * each of its kernel phases on the caller's stream (up to 4096 phases between

@@ -116,6 +116,11 @@ def load(build_if_missing: bool = False):
         lib.enkf_rblock_whiten.restype = ctypes.c_int
         lib.enkf_rblock_unwhiten.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp]
         lib.enkf_rblock_unwhiten.restype = ctypes.c_int
+        lib.enkf_ism_pivot_workspace.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
+        lib.enkf_ism_pivot_workspace.restype = ctypes.c_int
+        lib.enkf_ism_solve_pivot.argtypes = [i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, sz, vp,
+                                             ctypes.POINTER(i32)]
+        lib.enkf_ism_solve_pivot.restype = ctypes.c_int
         lib.enkf_ism_batch_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(enkf_ism_problem), i32, u32,
                                             ctypes.POINTER(sz)]
         lib.enkf_ism_batch_plan.restype = ctypes.c_int
@@ -310,6 +315,27 @@ def enkf_rblock_unwhiten(bs: int, Lblk, Z, stream=None) -> None:
     pZ, ldz = _mat(Z, "Z")
     ncols, nobs = Z.shape
     _check(load().enkf_rblock_unwhiten(nobs, ncols, _precision(Z), bs, _ptr(Lblk, "Lblk"), pZ, ldz, _stream(stream)))
+
+
+def enkf_ism_pivot_workspace(nobs: int, nens: int, precision: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().enkf_ism_pivot_workspace(nobs, nens, precision, ctypes.byref(b)))
+    return b.value
+
+
+def enkf_ism_solve_pivot(r, V, D, Z, workspace, M=None, perm=None, gamma=None, stream=None, sync: bool = True) -> int:
+    """Solve with the pivoting of Sec. 3.4.  V, D, Z: (nens, nobs); M: nens*nens (nullable); perm: int32 (nens);
+    gamma: float64 (nens).  Returns the device status word when ``sync``."""
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    pZ, ldz = _mat(Z, "Z")
+    nens, nobs = V.shape
+    st = ctypes.c_int32(0)
+    _check(load().enkf_ism_solve_pivot(nobs, nens, _precision(V), _ptr(r, "r"), pV, ldv, pD, ldd, pZ, ldz,
+                                       _ptr(M, "M"), _ptr(perm, "perm"), _ptr(gamma, "gamma"),
+                                       _ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                                       _stream(stream), ctypes.byref(st) if sync else None))
+    return st.value
 
 
 def enkf_ism_batch_plan(problems, mode: int = ENKF_FP32, flags: int = 0):
