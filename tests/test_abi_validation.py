@@ -1,0 +1,125 @@
+"""Host-side argument checks of the entry points beside the analysis (inflation, partial
+localization, block-diagonal R, pivoted solve), run on the CPU: every call here is rejected by
+the library's validation before it touches the GPU, so placeholder device addresses (never
+dereferenced) stand in for arrays.  Also the workspace sizing of the pivoted solve."""
+import ctypes
+import math
+
+import pytest
+
+from paper_1302_3876_gb300 import build as libbuild
+from paper_1302_3876_gb300 import enkf
+
+FP64, FP32 = enkf.ENKF_FP64, enkf.ENKF_FP32
+ARG, SHAPE, WS = enkf.ENKF_ERR_ARG, enkf.ENKF_ERR_SHAPE, enkf.ENKF_ERR_WORKSPACE
+
+# 256-byte aligned placeholder addresses, far apart (no overlap unless a test wants one)
+A0, A1, A2, A3, A4, A5 = (ctypes.c_void_p(0x100000000 * (k + 1)) for k in range(6))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return enkf.load()
+
+
+def _err(lib):
+    return lib.enkf_last_error().decode()
+
+
+def _loc(lib, nstate=64, nobs=32, nens=8, prec=FP32, stride=2, length=10.0, radius=-1.0, dXB=A0, ldx=None, V=A1,
+         ldv=None, Z=A2, ldz=None, XB=A3, ldb=None, XA=A4, lda=None):
+    return lib.enkf_localized_update(nstate, nobs, nens, prec, stride, length, radius, dXB, ldx or nstate, V,
+                                     ldv or nobs, Z, ldz or nobs, XB, ldb or nstate, XA, lda or nstate, None)
+
+
+def test_localized_update_rejects_bad_arguments(lib):
+    assert _loc(lib, nens=257) == SHAPE and "nens" in _err(lib)
+    assert _loc(lib, nens=1) == SHAPE
+    assert _loc(lib, prec=7) == ARG
+    assert _loc(lib, length=0.0) == ARG
+    assert _loc(lib, length=-3.0) == ARG
+    assert _loc(lib, radius=math.nan) == ARG
+    assert _loc(lib, nobs=40) == SHAPE                      # (nobs - 1) * stride >= nstate
+    assert _loc(lib, lda=63) == SHAPE
+    assert _loc(lib, ldv=31) == SHAPE
+    assert _loc(lib, dXB=None) == ARG
+    assert _loc(lib, XA=ctypes.c_void_p(0x100000002)) == ARG   # not aligned to 4 bytes
+    assert _loc(lib, XA=A1) == ARG and "overlaps" in _err(lib)  # X_A on top of V
+    assert _loc(lib, XA=A2) == ARG                              # X_A on top of Z
+    assert _loc(lib, XA=A3, lda=100) == ARG                     # X_B's memory with another ld
+
+
+def _infl(lib, nstate=64, nobs=16, nens=8, prec=FP32, stride=4, alpha=1.1, XB=A0, dXB=A1, Y=A2, V=A3, D=A4,
+          ldb=None):
+    return lib.enkf_inflate_prep(nstate, nobs, nens, prec, stride, alpha, XB, ldb or nstate, dXB, nstate, Y, nobs, V,
+                                 nobs, D, nobs, None)
+
+
+def test_inflate_prep_rejects_bad_arguments(lib):
+    assert _infl(lib, alpha=-0.5) == ARG
+    assert _infl(lib, alpha=math.inf) == ARG
+    assert _infl(lib, nens=1) == SHAPE
+    assert _infl(lib, prec=3) == ARG
+    assert _infl(lib, XB=None) == ARG
+    assert _infl(lib, D=None) == ARG                            # Y given without D
+    assert _infl(lib, nobs=17) == SHAPE                         # observed rows beyond the state
+    assert _infl(lib, ldb=10) == SHAPE
+
+
+def test_rblock_entry_points_reject_bad_arguments(lib):
+    assert lib.enkf_rblock_factor(100, 33, A0, A1, None) == SHAPE
+    assert lib.enkf_rblock_factor(100, 0, A0, A1, None) == SHAPE
+    assert lib.enkf_rblock_factor(0, 4, A0, A1, None) == SHAPE
+    assert lib.enkf_rblock_factor(100, 4, None, A1, None) == ARG
+    assert lib.enkf_rblock_factor(100, 4, A0, A0, None) == ARG and "overlap" in _err(lib)
+    assert lib.enkf_rblock_factor(100, 4, A0, ctypes.c_void_p(0x200000004), None) == ARG
+    assert lib.enkf_rblock_whiten(100, 8, 9, 4, A0, A1, 100, A2, 100, None) == ARG
+    assert lib.enkf_rblock_whiten(100, 0, FP32, 4, A0, A1, 100, A2, 100, None) == SHAPE
+    assert lib.enkf_rblock_whiten(100, 8, FP32, 4, A0, A1, 99, A2, 100, None) == SHAPE
+    assert lib.enkf_rblock_whiten(100, 8, FP64, 4, A0, ctypes.c_void_p(0x200000004), 100, A2, 100, None) == ARG
+    assert lib.enkf_rblock_whiten(100, 8, FP32, 64, A0, A1, 100, A2, 100, None) == SHAPE
+    assert lib.enkf_rblock_unwhiten(100, 0, FP32, 4, A0, A1, 100, None) == SHAPE
+    assert lib.enkf_rblock_unwhiten(100, 8, FP32, 4, None, A1, 100, None) == ARG
+    assert lib.enkf_rblock_unwhiten(100, 8, FP32, 4, A0, A1, 50, None) == SHAPE
+
+
+def _ws(lib, nobs, nens, prec):
+    b = ctypes.c_size_t()
+    st = lib.enkf_ism_pivot_workspace(nobs, nens, prec, ctypes.byref(b))
+    return st, b.value
+
+
+def test_pivot_workspace_sizes(lib):
+    assert _ws(lib, 1000, 257, FP32)[0] == SHAPE
+    assert _ws(lib, 0, 8, FP32)[0] == SHAPE
+    assert _ws(lib, 1000, 8, 4)[0] == ARG
+    st, b1 = _ws(lib, 1000, 32, FP32)
+    assert st == 0 and b1 % 256 == 0
+    # grows with the rows and the members; FP64 storage of U needs more
+    assert _ws(lib, 100000, 32, FP32)[1] > b1
+    assert _ws(lib, 1000, 64, FP32)[1] > b1
+    assert _ws(lib, 1000, 32, FP64)[1] > b1
+    # at least U (nobs x nens, ld padded to 32 rows) and the nens x nens factor arrays
+    nobs, nens = 12345, 100
+    assert _ws(lib, nobs, nens, FP32)[1] >= 4 * ((nobs + 31) // 32 * 32) * nens + 3 * 8 * nens * nens
+
+
+def _piv(lib, nobs=1000, nens=8, prec=FP32, Z=A3, M=A4, ws=A5, ws_bytes=None, ldz=None):
+    if ws_bytes is None:
+        ws_bytes = _ws(lib, nobs, min(nens, 256), FP32 if prec not in (FP32, FP64) else prec)[1]
+    st = ctypes.c_int32(0)
+    return lib.enkf_ism_solve_pivot(nobs, nens, prec, A0, A1, nobs, A2, nobs, Z, ldz or nobs, M, None, None, ws,
+                                    ws_bytes, None, ctypes.byref(st))
+
+
+def test_pivoted_solve_rejects_bad_arguments(lib):
+    assert _piv(lib, nens=257) == SHAPE
+    assert _piv(lib, nens=1) == SHAPE                           # M needs nens >= 2
+    assert _piv(lib, prec=2) == ARG
+    assert _piv(lib, Z=None) == ARG
+    assert _piv(lib, ldz=999) == SHAPE
+    assert _piv(lib, Z=A1) == ARG and "overlaps" in _err(lib)   # Z on top of V
+    assert _piv(lib, ws_bytes=1024) == WS
+    assert _piv(lib, ws=ctypes.c_void_p(0x600000010)) == WS     # not 256-byte aligned
+    assert _piv(lib, M=ctypes.c_void_p(0x500000002)) == ARG
