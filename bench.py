@@ -9,9 +9,15 @@ ABI: V = H dX_B / sqrt(Nens-1) on the device, Step 1 + Step 2 of the iterative
 Sherman-Morrison formula, M = V^T Z / sqrt(Nens-1), X_A = X_B + dX_B M.  Inputs
 (1.3 GB) are larger than L2, so no flush is needed between steps.
 
-The headline path is the FP32 plain level-streaming path; the FP64 plain path
-is timed in the same run as the comparator.  ``--impl reference`` times the
-FP64 CPU oracle instead (bounded sample of the same workload).
+The headline path is the panel form on FP32 CUDA cores (32 levels per pass,
+FP64 denominators; ``--mode`` selects the tensor-core panel variants or the plain
+FP32 level-streaming path); the FP64 plain path is timed in the same run as the
+comparator.  ``--impl reference`` times the FP64 CPU oracle instead (bounded
+sample of the same workload).  Other workloads (``--workload``): the panel
+workload at Nstate 2^22 / Nobs 2^20 / 256 members, the batched local analyses,
+the Lorenz-96 cycle with the learned surrogate, and the rows beside the analysis
+(inflation, partial localization, block-diagonal R, pivoting); each prints its
+own JSON line.
 
 Prints ONE JSON line on rank 0.
 """
@@ -467,7 +473,7 @@ def run_ours(args):
 
 # ---------------------------------------------------------------------------
 # Other workloads (not the default line): the panel workload, the batched
-# workload and the Lorenz-96 cycle with the learned surrogate.
+# workload, the Lorenz-96 cycle with the learned surrogate, and the next rows.
 # ---------------------------------------------------------------------------
 
 def _events_ms(fn, k):
