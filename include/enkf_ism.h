@@ -62,7 +62,7 @@ typedef enum {
     ENKF_ERR_CUDA = 3,        /* a CUDA runtime call failed (see enkf_last_error) */
     ENKF_ERR_NUMERIC = 4,     /* r_j <= 0, a non-finite value, or gamma_k < 1 - tol (Sec. 3.3) */
     ENKF_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
-    ENKF_ERR_UNSUPPORTED = 6, /* mode / size combination this build does not implement */
+    ENKF_ERR_UNSUPPORTED = 6, /* mode / size combination the library does not implement */
     ENKF_ERR_WORKSPACE = 7    /* workspace NULL, too small or not 256-byte aligned */
 } enkf_status;
 
