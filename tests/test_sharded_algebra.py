@@ -94,3 +94,67 @@ def test_row_sharded_recurrence_matches_the_oracle():
     np.testing.assert_allclose(gamma, ref["gamma"], rtol=1e-12)
     assert rel(M, ref["M"]) <= 1e-12
     assert rel(XA, ref["XA"]) <= 1e-12
+
+
+def _panel_worker(rank, world, port, q, b):
+    """The panel form of the recurrence (b levels per exchange): per panel P the ranks sum
+    G = V_P^T U_P (b x b) and A = V_P^T [U_trailing, Z] (b x ncols) in one all-reduce; the b x b
+    factor is then the same on every rank (gamma_m = 1 + (G beta_m)_m, h_m = U_P beta_m / gamma_m,
+    beta_j -= (beta_m / gamma_m)(G beta_j)_m), and each rank applies X -= U_P B (I + L)^{-1} A to its
+    rows, L the strictly lower part of G B."""
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    XB, dXB, r, D = _problem()
+    per = (NOBS + world - 1) // world
+    j0, j1 = rank * per, min(NOBS, (rank + 1) * per)
+    scale = 1.0 / math.sqrt(NENS - 1)
+    V = dXB[:, j0 * STRIDE:NSTATE:STRIDE][:, : j1 - j0] * scale
+    Dl, rl = D[:, j0:j1], r[j0:j1]
+    U, Z = V / rl, Dl / rl
+    gamma = np.zeros(NENS)
+    for k0 in range(0, NENS, b):
+        bp = min(b, NENS - k0)
+        P = slice(k0, k0 + bp)
+        X = np.concatenate([U[k0 + bp:], Z])                 # trailing columns of U, then Z
+        red = _allreduce(np.concatenate([(V[P] @ U[P].T).ravel(), (V[P] @ X.T).ravel()]))
+        G = red[: bp * bp].reshape(bp, bp)                   # G[l, m] = v_l^T u_m
+        A = red[bp * bp:].reshape(bp, X.shape[0])            # A[l, c] = v_l^T x_c
+        beta = np.eye(bp)                                    # u_m (current) = U_P beta[:, m]
+        B = np.zeros((bp, bp))
+        for m in range(bp):
+            gamma[k0 + m] = 1.0 + (G @ beta[:, m])[m]
+            B[:, m] = beta[:, m] / gamma[k0 + m]
+            for j in range(m + 1, bp):
+                beta[:, j] -= B[:, m] * (G @ beta[:, j])[m]
+        L = np.tril(G @ B, -1)
+        C = np.linalg.solve(np.eye(bp) + L, A)               # the level coefficients c = (I + L)^{-1} a
+        X = X - (U[P].T @ (B @ C)).T
+        U[k0 + bp:] = X[: NENS - k0 - bp]
+        Z = X[NENS - k0 - bp:]
+    zs = [None] * world
+    dist.all_gather_object(zs, Z)
+    if rank == 0:
+        q.put((np.concatenate(zs, axis=1), gamma))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("b", [1, 3, 7])
+def test_row_sharded_panel_recurrence_matches_the_oracle(b):
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 32500 + (os.getpid() + 17 * b) % 1000
+    procs = [ctx.Process(target=_panel_worker, args=(rk, 2, port, q, b)) for rk in range(2)]
+    for p in procs:
+        p.start()
+    Z, gamma = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    XB, dXB, r, D = _problem()
+    V = oracle.observe_deviations(dXB, NOBS, STRIDE)
+    Zref, gref = oracle.ism_solve(r, V, D, return_gamma=True)
+    assert np.linalg.norm(Z - Zref) / np.linalg.norm(Zref) <= 1e-12
+    np.testing.assert_allclose(gamma, gref, rtol=1e-12)
