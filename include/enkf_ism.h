@@ -27,7 +27,8 @@
  *   by enkf_ism_plan().  The one exception is enkf_ism_plan() itself, which
  *   allocates nothing on the device either (it only queries device properties).
  * - Element type follows the plan's mode: ENKF_FP64 means every floating-point
- *   buffer is double; every other mode uses float storage.
+ *   buffer is double; every other mode uses float storage.  Entry points that take
+ *   no plan take a precision argument (ENKF_FP64 or ENKF_FP32) instead.
  * - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
  *   void*; NULL is the legacy default stream).  Device-side checks (r_j <= 0,
  *   non-finite values, gamma_k < 1 - tol, an expired bounded wait) latch a status
