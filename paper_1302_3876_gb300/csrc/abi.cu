@@ -55,7 +55,7 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        off_delta, off_P, off_Md, off_vp, off_up, total;
+        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, total;
     int64_t ldp;              // row pitch of the 16-bit operand pieces (tensor-core panel modes)
     bool refine;
     // latched status of the previous call
@@ -180,6 +180,7 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
         p->off_delta = o; o = align256(o + sizeof(float) * (size_t)p->ldzw * N);
         p->off_P = o; o = align256(o + sizeof(double) * N * N);
         p->off_Md = o; o = align256(o + sizeof(double) * N * N);
+        p->off_rnorm = o; o = align256(o + sizeof(double) * 1040);   // residual-norm partials + result
     }
     p->total = o;
     e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
@@ -235,6 +236,16 @@ enkf_status enkf_ism_profile_read(enkf_ism_plan_t p, double* ms, int32_t* count)
         }
     }
     p->nprof = 0;
+    return ENKF_OK;
+}
+
+enkf_status enkf_ism_gamma(enkf_ism_plan_t p, const void* workspace, double* gamma) {
+    if (!p || !workspace || !gamma) return fail(ENKF_ERR_ARG, "enkf_ism_gamma: NULL argument");
+    CU(cudaSetDevice(p->device), "cudaSetDevice");
+    if (p->pending) CU(cudaEventSynchronize(p->done), "cudaEventSynchronize");
+    CU(cudaMemcpy(gamma, (const char*)workspace + p->off_gamma, sizeof(double) * (size_t)p->nens,
+                  cudaMemcpyDeviceToHost),
+       "enkf_ism_gamma: copy");
     return ENKF_OK;
 }
 
@@ -395,11 +406,27 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             double* Pd = (double*)(ws + p->off_Md);
             double* part = (double*)(ws + p->off_Qpart);
             float* delta = (float*)(ws + p->off_delta);
-            CU(gram_comp(p->nobs, p->nens, (const float*)V, ldv, (const float*)Zp, ldzp, part, p->nsplit, P, s),
-               "refine Gram V^T Z");
+            {
+                // fixed-point digits on the tensor cores when V and Z are TMA-aligned, else
+                // compensated FP32 sums on CUDA cores
+                cudaError_t eg = gram_exact(p->nobs, p->nens, (const float*)V, ldv, (const float*)Zp, ldzp, part,
+                                            p->nsplit, P, ctl, a.timeout_ns, s);
+                if (eg == cudaErrorNotSupported) {
+                    (void)cudaGetLastError();
+                    eg = gram_comp(p->nobs, p->nens, (const float*)V, ldv, (const float*)Zp, ldzp, part, p->nsplit,
+                                   P, s);
+                }
+                CU(eg, "refine Gram V^T Z");
+            }
+            // Mp (M's output, written last by refine_apply) holds -P in FP32 until then
             CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
-                               (const float*)Zp, ldzp, P, delta, p->ldzw, s),
+                               (const float*)Zp, ldzp, P, (float*)Mp, ws + p->off_Msplit, delta, p->ldzw, ctl,
+                               a.timeout_ns, s),
                "refine residual");
+            if (info)
+                CU(refine_resid_norm(p->nobs, p->nens, delta, p->ldzw, (const float*)r, (const float*)D, ldd,
+                                     (double*)(ws + p->off_rnorm), (double*)(ws + p->off_rnorm) + 1024, s),
+                   "refine residual norm");
             CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
                "refine Gram V^T U");
             PanelArgs ra = panel_args;
@@ -422,7 +449,8 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                 CU(xa_update(true, p->nstate, p->nens, XB, ldb, dXB, ldx, Mp, XA, lda, s), "xa_update launch");
             else
                 CU(xa_update_tc05(p->nstate, p->nens, (const float*)XB, ldb, (const float*)dXB, ldx, (const float*)Mp,
-                                  ws + p->off_Msplit, (float*)XA, lda, ctl, a.timeout_ns, s),
+                                  ws + p->off_Msplit, (float*)XA, lda, nullptr, p->refine ? 3 : 2, ctl,
+                                  a.timeout_ns, s),
                    "xa_update_tc05 launch");
             prof_end(p, slot, s);
         }
@@ -455,6 +483,12 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         free(g);
         info->gamma_min = gmin;
         info->gamma_max = gmax;
+        info->refine_resid = 0.0;
+        if (p->refine) {
+            e = cudaMemcpy(&info->refine_resid, (double*)(ws + p->off_rnorm) + 1024, sizeof(double),
+                           cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "refine residual norm copy");
+        }
         if (st != 0) {
             Control hc;
             cudaMemcpy(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost);

@@ -120,15 +120,25 @@ cudaError_t gram_full(bool fp64, int64_t nrows, int32_t n, const void* A, int64_
 //   gram_comp:       P[k][m] = sum_j A[j,k] B[j,m] (every k, m; row-major) with exact
 //                    products and compensated sums folded into FP64 (same splitting and
 //                    fixed-order reduction as gram_full; part holds nsplit * n * n doubles);
-//   refine_residual: delta = (D - r o Z - V P) / r with P = V^T Z (row-major P[m][i]),
-//                    the N-term sums with exact products and compensated FP32 sums;
+//   refine_residual: delta = (D - r o Z - V P) / r with P = V^T Z (row-major P[m][i]):
+//                    T = D - r o Z by FP32 FMAs, then the tensor-core X_A update with
+//                    -P (rounded to FP32 into Mneg, n * n floats; its split images in
+//                    msplit, xa_split_bytes(n) bytes) and the divisor r per row;
 //   refine_apply:    Z += delta and M = (P + Pd) / sqrt(n - 1) (column-major M[k + i n],
 //                    written to M64 and/or M when not NULL).
 cudaError_t gram_comp(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
                       double* part, int32_t nsplit, double* P, cudaStream_t s);
+// The same P on tcgen05 tensor cores from fixed-point BF16 digits (three per value, scaled per
+// 32-row chunk and column, exact level sums folded into double FP32; ~2^-32 of sum |a||b|).
+// cudaErrorNotSupported when A or B is not TMA-aligned (16-byte base and stride).
+cudaError_t gram_exact(int64_t nrows, int32_t n, const float* A, int64_t lda, const float* B, int64_t ldb,
+                       double* part, int32_t nsplit, double* P, Control* ctl, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t refine_residual(int64_t nobs, int32_t n, const float* r, const float* V, int64_t ldv, const float* D,
-                            int64_t ldd, const float* Z, int64_t ldz, const double* P, float* delta, int64_t ldo,
-                            cudaStream_t s);
+                            int64_t ldd, const float* Z, int64_t ldz, const double* P, float* Mneg, void* msplit,
+                            float* delta, int64_t ldo, Control* ctl, uint64_t timeout_ns, cudaStream_t s);
+// out[0] = ||delta||_F / ||D / r||_F (FP64, fixed-order; part: 1024 doubles of scratch).
+cudaError_t refine_resid_norm(int64_t nobs, int32_t n, const float* delta, int64_t ldd, const float* r,
+                              const float* D, int64_t ldD, double* part, double* out, cudaStream_t s);
 cudaError_t refine_apply(int64_t nobs, int32_t n, float* Z, int64_t ldz, const float* delta, int64_t ldd,
                          const double* P, const double* Pd, double* M64, float* M, cudaStream_t s);
 
@@ -145,9 +155,11 @@ cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, i
 // in TMEM); msplit: xa_split_bytes(nens) bytes of workspace (the split images of M);
 // waits are bounded by timeout_ns and latch kErrTimeout in ctl.
 size_t xa_split_bytes(int32_t nens);
+// rdiv (nullable): row i of the result is divided by rdiv[i].  pieces: 2 (hi + lo, three
+// products) or 3 (hi + mid + lo, six products).
 cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
-                           const float* M, void* msplit, float* XA, int64_t lda, Control* ctl, uint64_t timeout_ns,
-                           cudaStream_t s);
+                           const float* M, void* msplit, float* XA, int64_t lda, const float* rdiv, int pieces,
+                           Control* ctl, uint64_t timeout_ns, cudaStream_t s);
 
 // Observation-space preparation.
 cudaError_t obs_prep(bool fp64, int64_t nstate, int64_t nobs, int32_t nens, int32_t stride, int32_t center,

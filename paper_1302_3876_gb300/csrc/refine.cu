@@ -4,28 +4,31 @@
 //   delta0 = R^{-1} (D - (R + V V^T) Z1) = (D - r o Z1 - V P) / r,
 // the stored panel factors are applied to delta0 (refinement sweep of the panel
 // kernel) giving delta, and
-//   Z = Z1 + delta,   M = (V^T Z1 + V^T delta) / sqrt(N - 1).
+//   Z = Z1 + delta,   M = (V^T Z1 + V^T delta) / sqrt(N - 1) = (P + V^T delta) / sqrt(N - 1).
 //
-// M = V^T Z is ill-conditioned for a direct product: the part of Z in range(V) is
-// damped by 1/gamma (gamma ~ 10^4 at Nobs = 2^19), so an error e relative to
-// |v||z| in the Nobs-long sums becomes about gamma * e relative in M.  The Grams
-// here are therefore formed with exact products (TwoProd by FMA) and compensated
-// (Kahan) FP32 sums over blocks of 512 rows, the block sums and compensations
-// folded into FP64 -- about 2^-40 relative to |v||z| instead of 2^-24 sqrt(512).
-// The N-term sums V[j,:] P[:,i] of the residual use the same exact products and
-// compensated FP32 sums (P split into hi + lo floats).  FP64 arithmetic for either
-// would run on GB300's narrow FP64 pipe.  V^T delta needs no compensation: delta is
-// the small correction, so the plain Gram's relative error is scaled by |delta|/|Z|.
+// P must be accurate: the part of Z in range(V) is damped by 1/gamma (gamma ~ 10^4 at
+// Nobs = 2^19), so |P| is about 10^-6 of sum_j |v_j||z_j|, and an error e relative to that
+// sum becomes about 10^6 e relative in M.  The Gram P is therefore formed from
+// fixed-point BF16 digits on the tensor cores (gram_exact, ~2^-32 of that sum) or, when V
+// or Z is not TMA-aligned, here with exact products (TwoProd by FMA) and compensated
+// (Kahan) FP32 sums over blocks of 512 rows, the block sums and compensations folded into
+// FP64 (~2^-40).
+//
+// The residual's N-term sums V P need no such care.  The same P enters the residual
+// and M = P + V^T delta, so an error E in the product V P changes M only by
+// (I + V^T R^-1 V)^-1 V^T R^-1 E, damped by 1/gamma; it changes Z by R^-1 E-sized
+// amounts, so Z keeps its accuracy when E is ~1e-7 of sum |v||p|.  So T = D - r o Z1 is
+// one FP32 fused multiply-add per element, and (T - V P) / r runs on the tensor cores as
+// the X_A update (three BF16 pieces, six products, FP32 accumulation) with -P in place
+// of M and a divisor r per row.
+// V^T delta needs no compensation either: delta is the small correction, so the plain
+// Gram's relative error is scaled by |delta|/|Z|.
 #include <math.h>
 
 #include "internal.h"
 
 namespace enkf {
 namespace {
-
-constexpr int RCOL = 8;     // residual columns per CTA
-constexpr int RPT = 4;      // rows per thread
-constexpr int RM = 128;     // rows of P staged at a time
 
 // ---------------------------------------------------------------------------
 // Compensated Gram P[k][m] = sum_j A[j,k] B[j,m] (every k, m).  64 x 64 output tile
@@ -114,74 +117,63 @@ __global__ void gram_comp_reduce_kernel(int n, int nsplit, const double* __restr
     }
 }
 
-// Each thread forms RPT rows (j = row0 + t + 256 q) of RCOL residual columns; the
-// CTAs of one row block differ in blockIdx.x (the column group), so they run close
-// together and share V through L2.
-__global__ void __launch_bounds__(256) residual_kernel(int64_t nobs, int n, const float* __restrict__ r,
-                                                       const float* __restrict__ V, int64_t ldv,
-                                                       const float* __restrict__ D, int64_t ldd,
-                                                       const float* __restrict__ Z, int64_t ldz,
-                                                       const double* __restrict__ P, float* __restrict__ out,
-                                                       int64_t ldo) {
-    __shared__ __align__(16) float Ph[RM][RCOL];
-    __shared__ __align__(16) float Pl[RM][RCOL];
-    const int i0 = blockIdx.x * RCOL;
-    const int64_t row0 = (int64_t)blockIdx.y * (256 * RPT) + threadIdx.x;
-    // running sums of V[j,:] P[:,i]: sh (FP32, Kahan-compensated by sc) + sl (product
-    // errors and the lo part of P)
-    float sh[RPT][RCOL], sc[RPT][RCOL], sl[RPT][RCOL];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q)
-#pragma unroll
-        for (int c = 0; c < RCOL; ++c) sh[q][c] = 0.f, sc[q][c] = 0.f, sl[q][c] = 0.f;
-    for (int m0 = 0; m0 < n; m0 += RM) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < RM * RCOL; e += blockDim.x) {
-            const int m = e / RCOL, c = e % RCOL;
-            // P[m][i] = v_m^T z_i, row-major (m * n + i)
-            const double pv = (m0 + m < n && i0 + c < n) ? P[(int64_t)(m0 + m) * n + (i0 + c)] : 0.0;
-            const float h = (float)pv;
-            Ph[m][c] = h;
-            Pl[m][c] = (float)(pv - (double)h);
-        }
-        __syncthreads();
-        const int mmax = min(RM, n - m0);
-        for (int m = 0; m < mmax; ++m) {
-            float v[RPT];
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                const int64_t j = row0 + 256 * q;
-                v[q] = j < nobs ? V[(int64_t)(m0 + m) * ldv + j] : 0.f;
-            }
-#pragma unroll
-            for (int c = 0; c < RCOL; ++c) {
-                const float ph = Ph[m][c], pl = Pl[m][c];
-#pragma unroll
-                for (int q = 0; q < RPT; ++q) {
-                    const float p = __fmul_rn(v[q], ph);
-                    const float pe = __fmaf_rn(v[q], ph, -p);      // exact error of the product (TwoProd)
-                    const float y = __fsub_rn(p, sc[q][c]);
-                    const float t = __fadd_rn(sh[q][c], y);
-                    sc[q][c] = __fsub_rn(__fsub_rn(t, sh[q][c]), y);
-                    sh[q][c] = t;
-                    sl[q][c] = __fmaf_rn(v[q], pl, __fadd_rn(sl[q][c], pe));
-                }
-            }
-        }
+// T = D - r o Z1, one FP32 fused multiply-add per element (one rounding).
+__global__ void residual_prep_kernel(int64_t nobs, int n, const float* __restrict__ r, const float* __restrict__ D,
+                                     int64_t ldd, const float* __restrict__ Z, int64_t ldz, float* __restrict__ out,
+                                     int64_t ldo) {
+    const int64_t total = nobs * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / nobs);
+        const int64_t j = q % nobs;
+        out[(int64_t)i * ldo + j] = __fmaf_rn(-r[j], Z[(int64_t)i * ldz + j], D[(int64_t)i * ldd + j]);
     }
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int64_t j = row0 + 256 * q;
-        if (j >= nobs) break;
-        const double rj = (double)r[j];
-#pragma unroll
-        for (int c = 0; c < RCOL; ++c) {
-            const int i = i0 + c;
-            if (i >= n) break;
-            const double vp = ((double)sh[q][c] - (double)sc[q][c]) + (double)sl[q][c];
-            const double res = (double)D[(int64_t)i * ldd + j] - rj * (double)Z[(int64_t)i * ldz + j] - vp;
-            out[(int64_t)i * ldo + j] = (float)(res / rj);
+}
+
+// Mneg[k + i n] = -P[k][i] rounded to FP32 (P row-major FP64).
+__global__ void neg_p_kernel(int n, const double* __restrict__ P, float* __restrict__ Mneg) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(q % n), i = (int)(q / n);
+        Mneg[q] = (float)(-P[(int64_t)k * n + i]);
+    }
+}
+
+constexpr int kNormBlocks = 512;
+
+// Per-CTA FP64 sums of delta^2 and (D / r)^2 over a fixed share of the elements.
+__global__ void __launch_bounds__(256) resid_norm_kernel(int64_t nobs, int n, const float* __restrict__ delta,
+                                                         int64_t ldd, const float* __restrict__ r,
+                                                         const float* __restrict__ D, int64_t ldD,
+                                                         double* __restrict__ part) {
+    __shared__ double red[2][256];
+    const int64_t total = nobs * n;
+    double a = 0.0, b = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(q / nobs);
+        const int64_t j = q % nobs;
+        const double x = (double)delta[(int64_t)i * ldd + j];
+        const double y = (double)D[(int64_t)i * ldD + j] / (double)r[j];
+        a += x * x;
+        b += y * y;
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = red[0][0], part[2 * blockIdx.x + 1] = red[1][0];
+}
+
+__global__ void resid_norm_final_kernel(const double* __restrict__ part, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < kNormBlocks; ++q) a += part[2 * q], b += part[2 * q + 1];
+        out[0] = b > 0.0 ? sqrt(a / b) : 0.0;
     }
 }
 
@@ -224,10 +216,27 @@ cudaError_t gram_comp(int64_t nrows, int32_t n, const float* A, int64_t lda, con
 }
 
 cudaError_t refine_residual(int64_t nobs, int32_t n, const float* r, const float* V, int64_t ldv, const float* D,
-                            int64_t ldd, const float* Z, int64_t ldz, const double* P, float* delta, int64_t ldo,
-                            cudaStream_t s) {
-    dim3 grid((unsigned)((n + RCOL - 1) / RCOL), (unsigned)((nobs + 256 * RPT - 1) / (256 * RPT)));
-    residual_kernel<<<grid, 256, 0, s>>>(nobs, n, r, V, ldv, D, ldd, Z, ldz, P, delta, ldo);
+                            int64_t ldd, const float* Z, int64_t ldz, const double* P, float* Mneg, void* msplit,
+                            float* delta, int64_t ldo, Control* ctl, uint64_t timeout_ns, cudaStream_t s) {
+    int64_t blocks = (nobs * n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    residual_prep_kernel<<<(int)blocks, 256, 0, s>>>(nobs, n, r, D, ldd, Z, ldz, delta, ldo);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nn = (int64_t)n * n;
+    neg_p_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(n, P, Mneg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // delta = (T + V (-P)) / r on the tensor cores, written over T
+    return xa_update_tc05(nobs, n, delta, ldo, V, ldv, Mneg, msplit, delta, ldo, r, 3, ctl, timeout_ns, s);
+}
+
+cudaError_t refine_resid_norm(int64_t nobs, int32_t n, const float* delta, int64_t ldd, const float* r,
+                              const float* D, int64_t ldD, double* part, double* out, cudaStream_t s) {
+    resid_norm_kernel<<<kNormBlocks, 256, 0, s>>>(nobs, n, delta, ldd, r, D, ldD, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    resid_norm_final_kernel<<<1, 32, 0, s>>>(part, out);
     return cudaGetLastError();
 }
 

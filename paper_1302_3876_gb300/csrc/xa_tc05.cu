@@ -1,6 +1,9 @@
 // X_A = X_B + dX_B M (the SMEnKF analysis update, Sec. 3.1) on the fifth-generation
-// tensor cores: tcgen05.mma with BF16 operands split as x = hi + lo, three products
-// (hi*hi + hi*lo + lo*hi; lo*lo is below FP32 rounding), FP32 accumulators in TMEM.
+// tensor cores (with an optional divisor per row -- a product by its reciprocal -- the same
+// kernel forms the scaled refinement residual (T - V P) / r): tcgen05.mma with BF16 operands split into pieces,
+// x = hi + lo (three products hi*hi + hi*lo + lo*hi; operands kept to ~2^-17) or
+// x = hi + mid + lo (six products with i + j < 3; ~2^-25, FP32-class), FP32 accumulators in
+// TMEM.
 //
 // Persistent, warp-specialised CTA, one per SM; a tile is 128 state rows x NB members:
 //   warp 16     loader: TMA tensor copies of the FP32 dX_B chunk (128 rows x 32 members)
@@ -42,10 +45,10 @@ constexpr int XNMAX = 256;  // largest MMA N
 constexpr int kEpi = 256, kConv = 256;
 constexpr int kThreads = kEpi + kConv + 96;    // + loader warp + MMA warp + X_B loader warp
 constexpr int kRawBytes = XM * XKC * 4;        // one raw chunk
-constexpr int kABytes = 2 * XM * XKC * 2;      // A hi + lo of one chunk
+__host__ __device__ constexpr int a_bytes(int np) { return np * XM * XKC * 2; }   // A pieces of one chunk
 constexpr int kMaxSmem = 232448;
 
-__host__ __device__ constexpr int b_chunk_bytes(int nb) { return 2 * nb * XKC * 2; }   // B hi + lo of one chunk
+__host__ __device__ constexpr int b_chunk_bytes(int nb, int np) { return np * nb * XKC * 2; }   // B pieces of one chunk
 
 struct XaShared {
     uint64_t raw_full[XRS], raw_empty[XRS], a_full[4], a_empty[4], acc_full[2], acc_empty[2], drained;
@@ -82,23 +85,27 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// 8 consecutive k of one row -> hi and lo 16-byte rows of their core matrices.
+// 8 consecutive k of one row -> the NP pieces' 16-byte rows of their core matrices: piece q
+// is the BF16 rounding of what pieces 0..q-1 leave (the subtractions are exact in FP32).
+template <int NP>
 __device__ __forceinline__ void put_row8(unsigned char* ahi, int off, const float* v) {
-    uint4 h, l;
-    h.x = pack_bf16(v[0], v[1]);
-    h.y = pack_bf16(v[2], v[3]);
-    h.z = pack_bf16(v[4], v[5]);
-    h.w = pack_bf16(v[6], v[7]);
-    const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
-    float lo[8];
+    float rest[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) lo[q] = v[q] - __bfloat162float(hb[q]);
-    l.x = pack_bf16(lo[0], lo[1]);
-    l.y = pack_bf16(lo[2], lo[3]);
-    l.z = pack_bf16(lo[4], lo[5]);
-    l.w = pack_bf16(lo[6], lo[7]);
-    *reinterpret_cast<uint4*>(ahi + off) = h;
-    *reinterpret_cast<uint4*>(ahi + XM * XKC * 2 + off) = l;
+    for (int q = 0; q < 8; ++q) rest[q] = v[q];
+#pragma unroll
+    for (int pc = 0; pc < NP; ++pc) {
+        uint4 h;
+        h.x = pack_bf16(rest[0], rest[1]);
+        h.y = pack_bf16(rest[2], rest[3]);
+        h.z = pack_bf16(rest[4], rest[5]);
+        h.w = pack_bf16(rest[6], rest[7]);
+        *reinterpret_cast<uint4*>(ahi + pc * XM * XKC * 2 + off) = h;
+        if (pc + 1 < NP) {
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) rest[q] = rest[q] - __bfloat162float(hb[q]);
+        }
+    }
 }
 
 struct XaParams {
@@ -111,22 +118,24 @@ struct XaParams {
     const uint4* Mimg;
     float* XA;
     int64_t lda;
+    const float* rdiv;   // nullable: row i of the result is divided by rdiv[i]
     Control* ctl;
     uint64_t timeout_ns;
 };
 
-template <bool TMA>
+template <bool TMA, int NP>
 __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_constant__ CUtensorMap tmap,
                                                               const __grid_constant__ CUtensorMap tmapb, XaParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int nb = p.nb, nchunks = p.nchunks, nas = p.nas;
-    const int aslot = kABytes + (p.resident ? 0 : b_chunk_bytes(nb));
+    constexpr int kABytes = a_bytes(NP);
+    const int aslot = kABytes + (p.resident ? 0 : b_chunk_bytes(nb, NP));
     // 1024-byte aligned working area (the launch reserves 1 KB of slack for this)
     unsigned char* raw = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // XRS x kRawBytes
     unsigned char* xbs = raw + XRS * kRawBytes;                      // XBS x kRawBytes when p.xbt
     unsigned char* aring = xbs + (p.xbt ? XBS * kRawBytes : 0);     // nas x aslot
     unsigned char* bres = aring + nas * aslot;                       // resident B images
-    XaShared* sh = reinterpret_cast<XaShared*>(bres + (p.resident ? nchunks * b_chunk_bytes(nb) : 0));
+    XaShared* sh = reinterpret_cast<XaShared*>(bres + (p.resident ? nchunks * b_chunk_bytes(nb, NP) : 0));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int yb = blockIdx.y;
     const int64_t ntiles = (p.nstate + XM - 1) / XM;
@@ -182,9 +191,9 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
         const int ct = tid - kEpi;
         const int r = ct & (XM - 1), kh = ct >> 7;     // row, half of the chunk's 32 k
         if (p.resident) {
-            const uint4* src = p.Mimg + (int64_t)yb * nchunks * (b_chunk_bytes(nb) / 16);
+            const uint4* src = p.Mimg + (int64_t)yb * nchunks * (b_chunk_bytes(nb, NP) / 16);
             uint4* dst = reinterpret_cast<uint4*>(bres);
-            for (int q = ct; q < nchunks * b_chunk_bytes(nb) / 16; q += kConv) dst[q] = __ldg(src + q);
+            for (int q = ct; q < nchunks * b_chunk_bytes(nb, NP) / 16; q += kConv) dst[q] = __ldg(src + q);
         }
         int64_t g = 0;
         bool ok = true;
@@ -216,12 +225,12 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                 unsigned char* slot = aring + s * aslot;
                 // K-step kh, k-groups 0 and 1: core (r / 8, kg), row r % 8
                 const int off = kh * (XM * 32) + (r >> 3) * 256 + (r & 7) * 16;
-                put_row8(slot, off, v);
-                put_row8(slot, off + 128, v + 8);
+                put_row8<NP>(slot, off, v);
+                put_row8<NP>(slot, off + 128, v + 8);
                 if (!p.resident) {
-                    const uint4* src = p.Mimg + ((int64_t)yb * nchunks + c) * (b_chunk_bytes(nb) / 16);
+                    const uint4* src = p.Mimg + ((int64_t)yb * nchunks + c) * (b_chunk_bytes(nb, NP) / 16);
                     uint4* dst = reinterpret_cast<uint4*>(slot + kABytes);
-                    for (int q = ct; q < b_chunk_bytes(nb) / 16; q += kConv) dst[q] = __ldg(src + q);
+                    for (int q = ct; q < b_chunk_bytes(nb, NP) / 16; q += kConv) dst[q] = __ldg(src + q);
                 }
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive(&sh->a_full[s]);
@@ -267,9 +276,12 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                         tmem_wait_ld(acc);
                         const int e0 = yb * nb + gq * 16;
                         if (i < p.nstate) {
+                            // one reciprocal per row; a product by exactly 1 when there is no divisor
+                            const float rinv = p.rdiv ? 1.0f / p.rdiv[i] : 1.0f;
 #pragma unroll
                             for (int q = 0; q < 16; ++q)
-                                if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
+                                if (e0 + q < p.nens)
+                                    p.XA[(int64_t)(e0 + q) * p.lda + i] = (xb[q] + __uint_as_float(acc[q])) * rinv;
                         }
                     }
                     tc05::release_to_async(&sh->xb_empty[slot]);
@@ -296,9 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                 tmem_wait_ld(acc);
                 const int e0 = yb * nb + gq * 16;
                 if (i < p.nstate) {
+                    const float rinv = p.rdiv ? 1.0f / p.rdiv[i] : 1.0f;
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
-                        if (e0 + q < p.nens) p.XA[(int64_t)(e0 + q) * p.lda + i] = xb[q] + __uint_as_float(acc[q]);
+                        if (e0 + q < p.nens)
+                            p.XA[(int64_t)(e0 + q) * p.lda + i] = (xb[q] + __uint_as_float(acc[q])) * rinv;
                 }
             }
             tc_fence_before();
@@ -348,17 +362,21 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
                         break;
                     }
                     tc_fence_after();
-                    const unsigned char* ahi = aring + s * aslot;
-                    const unsigned char* alo = ahi + XM * XKC * 2;
-                    const unsigned char* bhi = p.resident ? bres + c * b_chunk_bytes(nb) : ahi + kABytes;
-                    const unsigned char* blo = bhi + nb * XKC * 2;
+                    const unsigned char* a0 = aring + s * aslot;
+                    const unsigned char* b0 = p.resident ? bres + c * b_chunk_bytes(nb, NP) : a0 + kABytes;
+                    // products of pieces (i, j) with i + j < NP, smallest first
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const int aoff = ks * XM * 32, boff = ks * nb * 32;
                         const int first = (c == 0 && ks == 0);
-                        mma_bf16(dcol, smem_desc(alo + aoff), smem_desc(bhi + boff), idesc, first ? 0 : 1);
-                        mma_bf16(dcol, smem_desc(ahi + aoff), smem_desc(blo + boff), idesc, 1);
-                        mma_bf16(dcol, smem_desc(ahi + aoff), smem_desc(bhi + boff), idesc, 1);
+                        int q = 0;
+#pragma unroll
+                        for (int sum = NP - 1; sum >= 0; --sum)
+#pragma unroll
+                            for (int i = sum; i >= 0; --i, ++q)
+                                mma_bf16(dcol, smem_desc(a0 + i * XM * XKC * 2 + aoff),
+                                         smem_desc(b0 + (sum - i) * nb * XKC * 2 + boff), idesc,
+                                         (first && q == 0) ? 0 : 1);
                     }
                     mma_commit(&sh->a_empty[s]);
                 }
@@ -381,8 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1) xa_tc05_kernel(const __grid_const
 }
 
 // M (column-major [k + e n]) -> the per-chunk canonical images: for column block yb
-// and chunk c, hi then lo, each [ks][n / 8][kg][n % 8][8 k] of BF16.
-__global__ void xa_tc05_image_kernel(const float* __restrict__ M, int n, int nb, int nblocks, int nchunks,
+// and chunk c, the np pieces in turn, each [ks][n / 8][kg][n % 8][8 k] of BF16.
+__global__ void xa_tc05_image_kernel(const float* __restrict__ M, int n, int nb, int nblocks, int nchunks, int np,
                                      __nv_bfloat16* __restrict__ img) {
     const int64_t per = (int64_t)nb * XKC;               // elements of one hi (or lo) chunk
     const int64_t total = (int64_t)nblocks * nchunks * per;
@@ -396,10 +414,12 @@ __global__ void xa_tc05_image_kernel(const float* __restrict__ M, int n, int nb,
         const int rn = r4 / 8, kk = r4 % 8;
         const int e = yb * nb + ng * 8 + rn;             // member (column of X_A)
         const int k = c * XKC + ks * 16 + kg * 8 + kk;   // member of dX_B (row of M)
-        const float v = (e < n && k < n) ? M[k + (int64_t)e * n] : 0.f;
-        const __nv_bfloat16 h = __float2bfloat16(v);
-        img[blk * 2 * per + rem] = h;
-        img[blk * 2 * per + per + rem] = __float2bfloat16(v - __bfloat162float(h));
+        float rest = (e < n && k < n) ? M[k + (int64_t)e * n] : 0.f;
+        for (int pc = 0; pc < np; ++pc) {
+            const __nv_bfloat16 h = __float2bfloat16(rest);
+            img[blk * np * per + pc * per + rem] = h;
+            rest = rest - __bfloat162float(h);
+        }
     }
 }
 
@@ -407,7 +427,7 @@ struct XaGeom {
     int nb, nblocks, nchunks, alloc, nas, resident, smem;
 };
 
-XaGeom xa_geom(int32_t nens, bool xbt) {
+XaGeom xa_geom(int32_t nens, bool xbt, int np) {
     XaGeom g;
     const int nfirst = nens < XNMAX ? nens : XNMAX;
     g.nb = (nfirst + 15) / 16 * 16;
@@ -416,9 +436,9 @@ XaGeom xa_geom(int32_t nens, bool xbt) {
     int alloc = 32;
     while (alloc < 2 * g.nb) alloc *= 2;
     g.alloc = alloc;
-    g.resident = g.nchunks * b_chunk_bytes(g.nb) <= 65536;
-    const int aslot = kABytes + (g.resident ? 0 : b_chunk_bytes(g.nb));
-    const int fixed = (XRS + (xbt ? XBS : 0)) * kRawBytes + (g.resident ? g.nchunks * b_chunk_bytes(g.nb) : 0) +
+    g.resident = g.nchunks * b_chunk_bytes(g.nb, np) <= 65536;
+    const int aslot = a_bytes(np) + (g.resident ? 0 : b_chunk_bytes(g.nb, np));
+    const int fixed = (XRS + (xbt ? XBS : 0)) * kRawBytes + (g.resident ? g.nchunks * b_chunk_bytes(g.nb, np) : 0) +
                       (int)sizeof(XaShared) + 1024;
     g.nas = (kMaxSmem - fixed) / aslot;
     if (g.nas > 4) g.nas = 4;
@@ -457,20 +477,21 @@ bool encode_f32_2d(CUtensorMap* map, const float* base, int64_t inner, int64_t o
 }
 
 size_t xa_split_bytes(int32_t nens) {
-    const XaGeom g = xa_geom(nens, false);
-    return (size_t)g.nblocks * g.nchunks * b_chunk_bytes(g.nb);
+    const XaGeom g = xa_geom(nens, false, 3);   // room for the three-piece images
+    return (size_t)g.nblocks * g.nchunks * b_chunk_bytes(g.nb, 3);
 }
 
 cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_t ldb, const float* dXB, int64_t ldx,
-                           const float* M, void* msplit, float* XA, int64_t lda, Control* ctl, uint64_t timeout_ns,
-                           cudaStream_t s) {
-    XaGeom g = xa_geom(nens, false);
+                           const float* M, void* msplit, float* XA, int64_t lda, const float* rdiv, int pieces,
+                           Control* ctl, uint64_t timeout_ns, cudaStream_t s) {
+    const int np = pieces == 3 ? 3 : 2;
+    XaGeom g = xa_geom(nens, false, np);
     if (g.nas < 2) return cudaErrorInvalidConfiguration;
     {
         const int64_t total = (int64_t)g.nblocks * g.nchunks * g.nb * XKC;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        xa_tc05_image_kernel<<<blocks, 256, 0, s>>>(M, nens, g.nb, g.nblocks, g.nchunks,
+        xa_tc05_image_kernel<<<blocks, 256, 0, s>>>(M, nens, g.nb, g.nblocks, g.nchunks, np,
                                                      static_cast<__nv_bfloat16*>(msplit));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -485,11 +506,12 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     const bool tma = encode_f32_2d(&tmap, dXB, nstate, nens, ldx, XM, XKC, false);
     bool xbt = tma && encode_f32_2d(&tmapb, XB, nstate, nens, ldb, XM, XKC, false);
     if (xbt) {
-        const XaGeom gx = xa_geom(nens, true);
+        const XaGeom gx = xa_geom(nens, true, np);
         if (gx.nas >= 2) g = gx;
         else xbt = false;
     }
-    const void* fn = tma ? (const void*)xa_tc05_kernel<true> : (const void*)xa_tc05_kernel<false>;
+    const void* fn = np == 3 ? (tma ? (const void*)xa_tc05_kernel<true, 3> : (const void*)xa_tc05_kernel<false, 3>)
+                             : (tma ? (const void*)xa_tc05_kernel<true, 2> : (const void*)xa_tc05_kernel<false, 2>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -515,6 +537,7 @@ cudaError_t xa_update_tc05(int64_t nstate, int32_t nens, const float* XB, int64_
     p.Mimg = static_cast<const uint4*>(msplit);
     p.XA = XA;
     p.lda = lda;
+    p.rdiv = rdiv;
     p.ctl = ctl;
     p.timeout_ns = timeout_ns;
     void* args[] = {&tmap, &tmapb, &p};
