@@ -103,6 +103,9 @@ typedef struct {
     int32_t grid_ctas;     /* CTAs of the level-streaming launch */
     int32_t status;        /* device status word of this call */
     int32_t reserved;
+    double refine_resid;   /* with ENKF_FLAG_REFINE: ||R^-1 (D - (R + V V^T) Z1)||_F / ||R^-1 D||_F of the
+                              solve's Z1 before the correction (the scaled residual the refinement
+                              applies the stored factors to); 0 without refinement */
 } enkf_ism_info;
 
 /*
@@ -388,6 +391,15 @@ ENKF_API enkf_status enkf_ism_solve_pivot(int64_t nobs, int32_t nens, int32_t pr
  * memory), and clears the record.  Phases: 0 obs prep, 1 level streaming (Step 1
  * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update, 5 refinement.
  */
+/*
+ * enkf_ism_gamma -- the level denominators gamma_k = 1 + v_k^T u_k^(k-1), k = 1..nens
+ * (Sec. 3.1, eq. SM-step-2-h; Theorem 2: gamma_k >= 1), of the last enkf_ism_analysis
+ * call made with this plan and workspace.  Waits for that call to finish, then copies
+ * nens doubles into gamma (caller-owned host memory).  Status codes only; no device
+ * memory is touched but the workspace's gamma entries.
+ */
+ENKF_API enkf_status enkf_ism_gamma(enkf_ism_plan_t plan, const void* workspace, double* gamma);
+
 #define ENKF_PROFILE_PHASES 8
 ENKF_API enkf_status enkf_ism_profile(enkf_ism_plan_t plan, int32_t enable);
 ENKF_API enkf_status enkf_ism_profile_read(enkf_ism_plan_t plan, double* ms, int32_t* count);
@@ -406,7 +418,13 @@ ENKF_API enkf_status enkf_ism_profile_read(enkf_ism_plan_t plan, double* ms, int
  *                 is the output.
  *   stream        cudaStream_t.
  *   status        host int or NULL; when given, the call synchronises the stream and
- *                 stores the device status word (0 = ok) there.
+ *                 stores the device status word (0 = ok) there, and returns that
+ *                 status when it is not 0.  With NULL the call stays asynchronous and
+ *                 device-side errors (r_j <= 0, non-finite values, gamma_k < 1 - tol,
+ *                 an expired bounded wait) are not reported at all: the next call
+ *                 clears the control block.  Unlike enkf_ism_analysis, nothing is
+ *                 latched for a later call, so a caller that must know whether Z is
+ *                 valid passes status.
  *
  * Scratch lives in one static device array of ENKF_NOALLOC_SCRATCH_BYTES (32 MiB)
  * that every GPU loading the library keeps until the process exits; the call
@@ -421,6 +439,19 @@ ENKF_API enkf_status enkf_ism_profile_read(enkf_ism_plan_t plan, double* ms, int
 ENKF_API enkf_status enkf_ism_solve_noalloc(int64_t nobs, int32_t nens, int32_t precision, const void* r,
                                             const void* V, int64_t ldv, const void* D, int64_t ldd,
                                             void* Z, int64_t ldz, void* stream, int32_t* status);
+
+/*
+ * enkf_fma_peak_launch -- launches a CUDA-core multiply-add microbenchmark on
+ * `stream`: every thread of ctas_per_sm (1..8) x SM-count CTAs of 256 threads runs
+ * 16 independent FMA chains of `iters` steps in registers.  The paper has no
+ * counterpart; it measures the FP32 and FP64 CUDA-core peaks against which the
+ * ALU-bound kernels are reported.  precision: ENKF_FP32 or ENKF_FP64.  sink: a
+ * device word of that type (never written in practice).  *flops (host) receives
+ * the exact number of floating-point operations of the launch (2 per FMA); the
+ * caller times the launch with CUDA events.
+ */
+ENKF_API enkf_status enkf_fma_peak_launch(int32_t precision, int32_t iters, int32_t ctas_per_sm, void* sink,
+                                          void* stream, double* flops);
 
 /* Human-readable name of a status code (static string). */
 ENKF_API const char* enkf_status_string(enkf_status s);

@@ -59,7 +59,8 @@ class enkf_ism_problem(ctypes.Structure):
 
 class enkf_ism_info(ctypes.Structure):
     _fields_ = [("gamma_min", ctypes.c_double), ("gamma_max", ctypes.c_double), ("panel_b", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("refine_resid", ctypes.c_double)]
 
 
 _lib = None
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = False):
         lib.enkf_ism_analysis.argtypes = [vp, vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, sz,
                                           vp, ctypes.POINTER(enkf_ism_info)]
         lib.enkf_ism_analysis.restype = ctypes.c_int
+        lib.enkf_ism_gamma.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.enkf_ism_gamma.restype = ctypes.c_int
         lib.enkf_ism_profile.argtypes = [vp, i32]
         lib.enkf_ism_profile.restype = ctypes.c_int
         lib.enkf_ism_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
@@ -137,6 +140,8 @@ def load(build_if_missing: bool = False):
         lib.enkf_surrogate_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, i64, i32, vp, sz, vp,
                                                   vp, vp]
         lib.enkf_surrogate_train_step.restype = ctypes.c_int
+        lib.enkf_fma_peak_launch.argtypes = [i32, i32, i32, vp, vp, ctypes.POINTER(dbl)]
+        lib.enkf_fma_peak_launch.restype = ctypes.c_int
         lib.enkf_status_string.argtypes = [ctypes.c_int]
         lib.enkf_status_string.restype = ctypes.c_char_p
         lib.enkf_last_error.argtypes = []
@@ -397,6 +402,13 @@ def enkf_surrogate_train_step(master, adam_m, adam_v, step, lr, packed, X, targe
                                             _ptr(grad, "grad"), _stream(stream)))
 
 
+def enkf_ism_gamma(plan, workspace, nens: int):
+    """The level denominators gamma_k of the plan's last analysis (list of nens floats)."""
+    g = (ctypes.c_double * nens)()
+    _check(load().enkf_ism_gamma(plan, _ptr(workspace, "workspace"), g))
+    return list(g)
+
+
 def enkf_ism_profile(plan, enable: bool) -> None:
     _check(load().enkf_ism_profile(plan, 1 if enable else 0))
 
@@ -407,6 +419,14 @@ def enkf_ism_profile_read(plan):
     cnt = (ctypes.c_int32 * ENKF_PROFILE_PHASES)()
     _check(load().enkf_ism_profile_read(plan, ms, cnt))
     return {PROFILE_PHASE_NAMES[i]: (ms[i], cnt[i]) for i in range(ENKF_PROFILE_PHASES) if cnt[i]}
+
+
+def enkf_fma_peak_launch(precision: int, iters: int, ctas_per_sm: int, sink, stream=None) -> float:
+    """Launch the CUDA-core FMA microbenchmark; returns the launch's flop count (time it with events)."""
+    fl = ctypes.c_double(0.0)
+    _check(load().enkf_fma_peak_launch(precision, iters, ctas_per_sm, _ptr(sink, "sink"), _stream(stream),
+                                       ctypes.byref(fl)))
+    return fl.value
 
 
 def enkf_status_string(status: int) -> str:
@@ -447,6 +467,9 @@ class Plan:
 
     def analysis(self, r, V, D, **kw):
         return enkf_ism_analysis(self.handle, r, V, D, self.workspace, **kw)
+
+    def gamma(self):
+        return enkf_ism_gamma(self.handle, self.workspace, self.nens)
 
     def obs_prep(self, obs_stride, center, XB, dXB, V, Y=None, D=None, stream=None):
         enkf_obs_prep(self.handle, obs_stride, center, XB, dXB, V, Y, D, stream)
