@@ -1,21 +1,14 @@
-"""Parity of the tensor-core panel forms with the FP64 oracle.
+"""Parity of the tensor-core panel forms and of the refinement with the FP64 oracle.
 
 ENKF_PANEL_BF16 runs the trailing update and the dots on tensor cores with split
 BF16 operands (x = hi + lo, three products; each operand kept to ~2^-17);
 ENKF_PANEL_FP16 uses one FP16 product (unit roundoff 2^-11); ENKF_PANEL_BF16X3 splits
 each operand in three BF16 pieces (six products, operands kept to ~2^-25, the FP32
 bars of the plain path).  All store in FP32, accumulate in FP32 and form the level
-denominators in FP64.  Tolerances WITHOUT
-refinement, stated per result (relative Frobenius error against the oracle on the
-same FP32 inputs; M = V^T Z carries the conditioning of R + V V^T, hence the
-gamma factor):
-
-    mode          Z       X_A      M
-    PANEL_BF16    1e-4    5e-5     2e-5 * max(1, gamma_max/10)
-    PANEL_FP16    5e-3    1e-3     2e-3 * max(1, gamma_max/10)
-    PANEL_BF16X3  1e-5    1e-5     1e-6 * max(1, gamma_max/10)
-
-The measured errors are printed so the tables in the design notes can quote them.
+denominators in FP64.  The bars are per result, fixed, from tests/bars.py (Z, X_A, M
+and the increment dX_B M, relative Frobenius error against the oracle on the same
+FP32 inputs).  The measured errors are printed so the tables in the design notes can
+quote them.
 """
 import math
 
@@ -24,6 +17,7 @@ import pytest
 
 import oracle
 import synth
+from tests import bars as B
 from tests.util import host, rel
 
 torch = pytest.importorskip("torch")
@@ -31,11 +25,6 @@ pytestmark = pytest.mark.gpu
 
 from paper_1302_3876_gb300 import enkf  # noqa: E402
 
-BARS = {
-    enkf.ENKF_PANEL_BF16: {"Z": 1e-4, "XA": 5e-5, "M": 2e-5},
-    enkf.ENKF_PANEL_FP16: {"Z": 5e-3, "XA": 1e-3, "M": 2e-3},
-    enkf.ENKF_PANEL_BF16X3: {"Z": 1e-5, "XA": 1e-5, "M": 1e-6},
-}
 NAME = {enkf.ENKF_PANEL_BF16: "PANEL_BF16", enkf.ENKF_PANEL_FP16: "PANEL_FP16",
         enkf.ENKF_PANEL_BF16X3: "PANEL_BF16X3"}
 # ~ 2^-17, 2^-11 and 2^-25 operands
@@ -75,26 +64,37 @@ def run(mode, r, V, D, dXB, panel_b=0, flags=0):
     return out
 
 
-def errors(dev, r, V, D, dXB):
+_REF = {}
+
+
+def reference(r, V, D, dXB):
+    """The oracle's Z, gamma, M and X_A (cached for the full-size workloads, which several
+    tests share)."""
+    key = (V.shape, float(r[0]), float(D[0, 0]), float(V[-1, -1]))
+    if key in _REF:
+        return _REF[key]
     Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
     M = oracle.vtz(V, Z)
-    XA = oracle.analysis_update(dXB, dXB, M)
+    out = (Z, gamma, M, oracle.analysis_update(dXB, dXB, M))
+    if V.shape[1] >= 200000:   # keep the latest full-size reference only
+        _REF.clear()
+        _REF[key] = out
+    return out
+
+
+def errors(dev, r, V, D, dXB):
+    Z, gamma, M, XA = reference(r, V, D, dXB)
     return {"Z": rel(dev["Z"], Z), "XA": rel(dev["XA"], XA), "M": rel(dev["M"], M),
             "increment": rel(dev["XA"] - dXB, XA - dXB)}, gamma
 
 
 def check(mode, dev, r, V, D, dXB, label):
-    Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
-    M = oracle.vtz(V, Z)
-    XA = oracle.analysis_update(dXB, dXB, M)
+    Z, gamma, M, XA = reference(r, V, D, dXB)
     errs = {"Z": rel(dev["Z"], Z), "XA": rel(dev["XA"], XA), "M": rel(dev["M"], M),
             "increment": rel(dev["XA"] - dXB, XA - dXB)}
     print(f"{NAME[mode]} {label}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()) +
           f", gamma_max {gamma.max():.1f}")
-    bar = BARS[mode]
-    assert errs["Z"] <= bar["Z"], errs
-    assert errs["XA"] <= bar["XA"], errs
-    assert errs["M"] <= bar["M"] * max(1.0, gamma.max() / 10.0), errs
+    B.check(errs, mode, label=f"{NAME[mode]} {label}")
     # the level denominators inherit the operand precision of the panel Gram
     assert dev["info"].gamma_max == pytest.approx(gamma.max(), rel=GAMMA_REL[mode])
 
@@ -136,12 +136,12 @@ def test_panel_single_full_size():
 # One step of iterative refinement (ENKF_FLAG_REFINE).  The correction applies the
 # stored factors, an approximate inverse whose error in range(V) is about
 # rho = u * gamma_max (u the precision of the solve's operands), so one step
-# multiplies the error of Z and M by about rho; M then comes from compensated
-# Grams of the refined Z.  Bars: PANEL_FP32 and PANEL_BF16 (rho < 0.1): X_A within
-# 1e-5 of the oracle, M within max(4e-6, 0.2 * before), Z within max(1e-7, 0.5 *
-# before).  PANEL_FP16 (u = 2^-11): the errors of Z and M must shrink where
-# rho < 1 (the medium cases below); at gamma ~ 10^4 it is not effective and is
-# not tested there.
+# multiplies the error of Z and M by about rho.  The refined FP32-class paths
+# (PANEL_FP32, PANEL_BF16X3) are held to 1e-5 on every result, split BF16 to its
+# refined bars (tests/bars.py), and every refined error must also be below the
+# unrefined one where that was above the refined floor.  PANEL_FP16 (u = 2^-11):
+# the errors of Z and M must shrink where rho < 1 (the medium cases below); at
+# gamma ~ 10^4 it is not effective and is not tested there.
 # ---------------------------------------------------------------------------
 GAIN_MODES = (enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP32, enkf.ENKF_PANEL_BF16X3)
 
@@ -158,9 +158,9 @@ def test_refinement_random(mode, nobs, nens, panel_b):
           ", ".join(f"{k} {v:.2e}" for k, v in base.items()) + " | after " +
           ", ".join(f"{k} {v:.2e}" for k, v in ref.items()))
     if mode in GAIN_MODES:
-        assert ref["XA"] <= 1e-5, ref
-        assert ref["M"] <= max(4e-6, 0.2 * base["M"]), (base, ref)
-        assert ref["Z"] <= max(1e-7, 0.5 * base["Z"]), (base, ref)
+        B.check(ref, mode, refine=True, label=f"refined {NAME.get(mode, mode)}")
+        for k in ("Z", "M", "increment"):
+            assert ref[k] <= max(2e-6, base[k]), (k, base, ref)
     else:
         assert ref["Z"] <= 0.1 * base["Z"], (base, ref)
         assert ref["M"] <= 0.5 * base["M"], (base, ref)
@@ -169,6 +169,7 @@ def test_refinement_random(mode, nobs, nens, panel_b):
 
 @pytest.mark.parametrize("mode", GAIN_MODES)
 def test_refinement_large_single_full_size(mode):
+    """Nstate 2^21, Nobs 2^19, Nens 128 (gamma ~ 8000): the refined paths at their bars."""
     w = synth.large_single(dtype=np.float32)
     dXB = w["dXB"].astype(np.float64)
     r = w["r"].astype(np.float64)
@@ -179,5 +180,21 @@ def test_refinement_large_single_full_size(mode):
     print(f"refine {mode} large_single gamma_max={gamma.max():.0f}: before " +
           ", ".join(f"{k} {v:.2e}" for k, v in base.items()) + " | after " +
           ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-    assert errs["XA"] <= 1e-5, errs
-    assert errs["M"] <= max(4e-6, 0.2 * base["M"]), (base, errs)
+    B.check(errs, mode, refine=True, label="refined large_single")
+    B.check(base, mode, refine=False, label="unrefined large_single")
+
+
+@pytest.mark.parametrize("mode", [enkf.ENKF_PANEL_FP32, enkf.ENKF_PANEL_BF16X3])
+def test_refinement_panel_single_full_size(mode):
+    """Nstate 2^22, Nobs 2^20, Nens 256: the refined FP32-class panel paths meet 1e-5 on Z,
+    M, X_A and the increment at the panel workload."""
+    w = synth.panel_single()
+    dXB = w["dXB"].astype(np.float64)
+    r = w["r"].astype(np.float64)
+    D = w["D"].astype(np.float64)
+    del w
+    V = oracle.observe_deviations(dXB, 1 << 20, 4).astype(np.float32).astype(np.float64)
+    errs, gamma = errors(run(mode, r, V, D, dXB, flags=enkf.ENKF_FLAG_REFINE), r, V, D, dXB)
+    print(f"refine {mode} panel_single gamma_max={gamma.max():.0f}: " +
+          ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    B.check(errs, mode, refine=True, label="refined panel_single")

@@ -6,15 +6,16 @@ unwhiten with enkf_ism_analysis).
 Tolerances (relative Frobenius norm): FP64 <= 1e-10; FP32 <= 1e-5 on X_A, Z and the
 prep outputs.  The localized increment dX_A = X_A - X_B on its own is held to 2e-5 in
 FP32: it is a sum over every observation of products formed with FP32 sums over the
-members, so its rounding error grows with sqrt(Nobs) relative to the increment.  M
-carries the conditioning of R + V V^T as in the plain-path tests: 1e-5 * max(1,
-gamma_max / 100) in FP32."""
+members, so its rounding error grows with sqrt(Nobs) relative to the increment.  The
+block-R analysis is held to the plain path's per-result bars (tests/bars.py): FP32 Z
+and X_A 1e-5, M and the increment 1e-4 without refinement."""
 import math
 
 import numpy as np
 import pytest
 
 import oracle
+from tests import bars as B
 import synth
 from tests.util import host, rel, rounded, to_dev, vec_dev
 
@@ -223,11 +224,9 @@ def test_block_diagonal_r_analysis_matches_oracle(prec, nobs, bs, nens):
     M = oracle.vtz(V, Z)
     XA = oracle.analysis_update(XB, dXB, M)
     assert inf.status == 0
-    assert rel(host(tZ), Z) <= tol
     assert inf.gamma_max == pytest.approx(gamma.max(), rel=10 * tol)
-    m_tol = tol * max(1.0, gamma.max() / 100.0)
-    assert rel(host(tM).reshape(nens, nens).T, M) <= m_tol
-    assert rel(host(tXA), XA) <= tol
+    B.check({"Z": rel(host(tZ), Z), "M": rel(host(tM).reshape(nens, nens).T, M), "XA": rel(host(tXA), XA),
+             "increment": rel(host(tXA) - XB, XA - XB)}, mode, label=f"block-R {prec} ({nobs}, {bs}, {nens})")
 
 
 def test_block_diagonal_r_not_positive_definite_is_reported():
