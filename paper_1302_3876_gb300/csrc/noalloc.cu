@@ -20,7 +20,9 @@
 // cudaGetSymbolAddress and caches it per device; make that first call before any
 // stream capture.  All calls share the one array, which keeps the last call's
 // contents: the control block is cleared on every call, and calls that overlap on
-// the GPU (two streams, or two host threads, at once) race on the scratch.
+// the GPU (two streams, or two host threads, at once) race on the scratch.  Device-
+// side errors reach the caller only through the optional status word (which makes
+// the call synchronous); with status NULL they are dropped, not latched.
 #include <stdarg.h>
 #include <stdio.h>
 

@@ -3,16 +3,23 @@
 Such callers (for example a plugin whose host application already owns the GPU
 memory through its own pool) cannot give enkf_ism_analysis a workspace.  The
 no-allocation entry point keeps its scratch in the library's static device
-array; this test checks, through the C ABI, that two calls in a row give the
-same Z as the workspace entry point, within the tolerance of the other parity
-tests (1e-10 FP64, 1e-5 FP32).  It lives in its own file, collected last, and
-runs alone in a fresh process as well as after the other tests.
+array; these tests check, through the C ABI, that two calls in a row give the
+same Z as the workspace entry point and as the FP64 oracle, within the
+tolerance of the other parity tests (1e-10 FP64, 1e-5 FP32), that an
+asynchronous call (no status word) gives the same Z once the stream is
+synchronised, and that a device-side error comes back through the status word.
+The file is collected last; one test also runs the file again in a fresh
+Python process, so that it is known to pass alone as well as after the others.
 """
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from tests.util import host, rel
 
@@ -61,6 +68,7 @@ def test_noalloc_matches_workspace_entry_twice(dt):
         assert enkf.enkf_ism_solve_noalloc(r, V, D, Z) == 0
         torch.cuda.synchronize()
         assert rel(host(Z), ref) <= TOL[dt]
+        assert rel(host(Z), oracle.ism_solve(host(r), host(V), host(D))) <= TOL[dt]
     # the same problem again: the scratch keeps the previous call's contents, the
     # result must not depend on them
     nobs, nens, seed = cases[0]
@@ -84,3 +92,39 @@ def test_noalloc_rejects_sizes_beyond_the_static_scratch():
         enkf.enkf_ism_solve_noalloc(r, V, D, Z)
     assert e.value.status == enkf.ENKF_ERR_WORKSPACE
     assert "static array" in str(e.value)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_noalloc_asynchronous_call(dt):
+    """status NULL: the call returns at once; after a synchronise Z equals the oracle's."""
+    nobs, nens = 5000, 24
+    r, V, D = problem(103, nobs, nens, dt)
+    Z = torch.full_like(D, float("nan"))
+    assert enkf.enkf_ism_solve_noalloc(r, V, D, Z, sync=False) == 0
+    torch.cuda.synchronize()
+    assert rel(host(Z), oracle.ism_solve(host(r), host(V), host(D))) <= TOL[dt]
+
+
+def test_noalloc_reports_a_numeric_error_through_the_status_word():
+    """A NaN innovation latches ENKF_ERR_NUMERIC on the device; the status word brings it back,
+    and the next call (valid data, same static array) succeeds."""
+    nobs, nens = 1000, 8
+    r, V, D = problem(104, nobs, nens, torch.float32)
+    Dbad = D.clone()
+    Dbad[3, 17] = float("nan")
+    Z = torch.empty_like(D)
+    with pytest.raises(enkf.EnkfError) as e:
+        enkf.enkf_ism_solve_noalloc(r, V, Dbad, Z)
+    assert e.value.status == enkf.ENKF_ERR_NUMERIC
+    assert enkf.enkf_ism_solve_noalloc(r, V, D, Z) == 0
+    assert rel(host(Z), oracle.ism_solve(host(r), host(V), host(D))) <= TOL[torch.float32]
+
+
+def test_noalloc_file_passes_alone_in_a_fresh_process():
+    if os.environ.get("ENKF_NOALLOC_CHILD"):
+        pytest.skip("already the fresh process")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, ENKF_NOALLOC_CHILD="1")
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
+                          os.path.abspath(__file__)], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
