@@ -69,9 +69,33 @@ def panel_bytes(nobs, nens, b, w):
     return w * nobs * cols
 
 
-def fp32_alu_peak_tflops(sm_count=152, lanes=128, mhz=2070.0):
-    """FP32 CUDA-core peak: SMs x FP32 lanes per SM x 2 flop per FMA x clock."""
-    return sm_count * lanes * 2 * mhz * 1e6 / 1e12
+def measure_fma_peaks(dev, local):
+    """FP32 and FP64 CUDA-core multiply-add peaks measured on this GPU by the library's own
+    microbenchmark (enkf_fma_peak_launch: 16 independent FMA chains per thread, 4 CTAs of 256
+    threads per SM), timed with CUDA events after a warm-up, the SM clock sampled meanwhile.
+    Returns {"fp32_tflops", "fp64_tflops", "sm_mhz", "how"}."""
+    import torch
+    from paper_1302_3876_gb300 import enkf
+    sink = torch.zeros(2, dtype=torch.float64, device=dev)
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, prec, iters in (("fp32_tflops", enkf.ENKF_FP32, 1 << 16), ("fp64_tflops", enkf.ENKF_FP64, 1 << 12)):
+            enkf.enkf_fma_peak_launch(prec, iters, 4, sink)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = float("inf")
+            flops = 0.0
+            for _ in range(5):
+                e0.record()
+                flops = enkf.enkf_fma_peak_launch(prec, iters, 4, sink)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = flops / (best / 1e3) / 1e12
+    out["sm_mhz"] = clk.summary().get("sm_mhz")
+    out["how"] = ("enkf_fma_peak_launch: 4 CTAs x 256 threads per SM, 16 independent FMA chains per thread, "
+                  "best of 5 launches by CUDA events")
+    return out
 
 
 def read_bf16_peak():
@@ -184,6 +208,9 @@ def dist_setup():
     return world, rank, local
 
 
+CPU_FRAC = {"panel_single": 5, "large_single": 3}   # row sample of the oracle: 1/2^k of the rows
+
+
 def cpu_oracle_sample(frac_log2: int, seconds: float, seed_offset: int = 0):
     """Times the FP64 oracle on a row sample of the workload: Nobs and Nstate divided
     by 2^frac_log2, Nens unchanged (cost is linear in Nobs and Nstate)."""
@@ -191,7 +218,8 @@ def cpu_oracle_sample(frac_log2: int, seconds: float, seed_offset: int = 0):
     import oracle
     import synth
     nobs, nstate = NOBS >> frac_log2, NSTATE >> frac_log2
-    w = synth.large_single(nstate, nobs, NENS, dtype=np.float64)
+    gen = synth.panel_single if NENS == 256 else synth.large_single
+    w = gen(nstate, nobs, NENS, dtype=np.float64)
     dXB, r, D = w["dXB"], w["r"], w["D"]
     oracle.build()
     runs, t0 = 0, time.perf_counter()
@@ -218,19 +246,24 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
+    if args.workload not in HEADLINE:
+        args.workload = "panel_single"
+    set_headline(args)
+    frac = CPU_FRAC[args.workload]
     per_step = []
     for _ in range(args.warmup):
-        cpu_oracle_sample(3, 0.0)
+        cpu_oracle_sample(frac, 0.0)
     sample = None
     for _ in range(args.steps):
-        sample = cpu_oracle_sample(3, 0.0)
-        per_step.append(sample["seconds_per_sample"] * 8)
+        sample = cpu_oracle_sample(frac, 0.0)
+        per_step.append(sample["seconds_per_sample"] * (1 << frac))
     value = args.steps / sum(per_step)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "1/8 of the rows per step, time scaled by 8"},
+        "config": {"workload": WORKLOAD, "sample": f"1/{1 << frac} of the rows per step; each step's time is "
+                                                   f"the sample's time x {1 << frac} (extrapolated)"},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": sample["cores"], "kind": "oracle",
                          "sample": sample["sample"]},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -238,12 +271,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    global NSTATE, NOBS, WORKLOAD
+HEADLINE = {
+    # name: (Nstate, Nobs, Nens, description)
+    "panel_single": (1 << 22, 1 << 20, 256, "panel_single Nstate=4194304 Nobs=1048576 Nens=256 "
+                     "(every 4th variable observed)"),
+    "large_single": (1 << 21, 1 << 19, 128, "large_single Nstate=2097152 Nobs=524288 Nens=128 "
+                     "(every 4th variable observed)"),
+}
+MODES = {"panel32": "ENKF_PANEL_FP32", "bf16": "ENKF_PANEL_BF16", "fp16": "ENKF_PANEL_FP16",
+         "bf16x3": "ENKF_PANEL_BF16X3", "fp32": "ENKF_FP32"}
+PATH_NAME = {"panel32": "panel form on FP32 CUDA cores, b=%d (FP64 gamma)",
+             "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)",
+             "bf16x3": "panel form on tensor cores, BF16 operands split in three, b=%d (FP64 gamma)",
+             "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)",
+             "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}
+
+
+def set_headline(args):
+    global NSTATE, NOBS, NENS, WORKLOAD
+    NSTATE, NOBS, NENS, WORKLOAD = HEADLINE[args.workload]
     if args.scale_div > 1:
         NSTATE //= args.scale_div
         NOBS //= args.scale_div
-        WORKLOAD = f"large_single/{args.scale_div} Nstate={NSTATE} Nobs={NOBS} Nens={NENS}"
+        WORKLOAD = f"{args.workload}/{args.scale_div} Nstate={NSTATE} Nobs={NOBS} Nens={NENS}"
+
+
+def run_ours(args):
+    set_headline(args)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -259,38 +313,43 @@ def run_ours(args):
     enkf.load(build_if_missing=True)
 
     # cpu baseline first (rank 0, before any large device allocation)
-    cpu = cpu_oracle_sample(3, args.cpu_seconds) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    cpu = cpu_oracle_sample(CPU_FRAC[args.workload], args.cpu_seconds) \
+        if (rank == 0 and world == 1 and not args.no_cpu) else None
+    peaks = measure_fma_peaks(dev, local)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = synth.large_single(NSTATE, NOBS, NENS, dtype=np.float32)
+    gen = synth.panel_single if args.workload == "panel_single" else synth.large_single
+    w = gen(NSTATE, NOBS, NENS, dtype=np.float32)
     h_dX = torch.from_numpy(w["dXB"]).pin_memory()
     h_D = torch.from_numpy(w["D"]).pin_memory()
     h_r = torch.from_numpy(w["r"]).pin_memory()
+    del w
     dX = h_dX.to(dev)
+    XB = dX.clone()     # the background (equal to the deviations, R-9), in a buffer of its own
     D = h_D.to(dev)
     r = h_r.to(dev)
     V = torch.empty(NENS, NOBS, dtype=torch.float32, device=dev)
+    Z = torch.empty(NENS, NOBS, dtype=torch.float32, device=dev)
     XA = torch.empty_like(dX)
     M = torch.empty(NENS * NENS, dtype=torch.float32, device=dev)
-    mode = {"panel32": enkf.ENKF_PANEL_FP32, "bf16": enkf.ENKF_PANEL_BF16, "fp16": enkf.ENKF_PANEL_FP16,
-            "bf16x3": enkf.ENKF_PANEL_BF16X3,
-            "fp32": enkf.ENKF_FP32}[args.mode]
+    mode = getattr(enkf, MODES[args.mode])
+    refine = args.refine and args.mode != "fp32"
     plan = enkf.Plan(NSTATE, NOBS, NENS, mode, panel_b=args.panel_b if args.mode != "fp32" else 0,
-                     flags=enkf.ENKF_FLAG_REFINE if args.refine else 0, device=dev)
+                     flags=enkf.ENKF_FLAG_REFINE if refine else 0, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
         plan.obs_prep(STRIDE, 0, None, dX, V)
-        plan.analysis(r, V, D, dXB=dX, XB=dX, XA=XA, M=M)
+        plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA, Z=Z, M=M)
 
     for _ in range(args.warmup):
         step()
     barrier()
-    inf = plan.analysis(r, V, D, dXB=dX, XB=dX, XA=XA, M=M, info=True)   # status check, untimed
+    inf = plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA, Z=Z, M=M, info=True)   # status check, untimed
     enkf.enkf_ism_profile(plan.handle, True)
     barrier()
     with ClockSampler(local) as clk:
@@ -307,46 +366,51 @@ def run_ours(args):
     t_max, value = aggregate_ranks(t_ms, args.steps, world, dev)
 
     # end to end through the API with host buffers, pipelined as a serving loop would run it: two
-    # sets of device buffers; step i's inputs are copied in on one stream while step i-1 computes,
-    # and step i-2's X_A is copied out on another.  Every step copies all of its inputs in from
-    # pinned host memory and its X_A out inside the timed region.
-    h_XA = [torch.empty(XA.shape, dtype=XA.dtype).pin_memory() for _ in range(2)]
-    bufs = [(dX, D, r, XA), (torch.empty_like(dX), torch.empty_like(D), torch.empty_like(r), torch.empty_like(XA))]
-    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    e2e_steps = max(2, min(args.steps, 10))
-
-    def e2e_run(nsteps):
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        start = torch.cuda.Event()
-        start.record(stream)
-        s_in.wait_event(start)
-        for i in range(nsteps):
-            b = i & 1
-            bdX, bD, br, bXA = bufs[b]
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev_done[b])      # step i-2 no longer reads these inputs
-                bdX.copy_(h_dX, non_blocking=True)
-                bD.copy_(h_D, non_blocking=True)
-                br.copy_(h_r, non_blocking=True)
-                ev_in[b].record(s_in)
-            stream.wait_event(ev_in[b])
-            if i >= 2:
-                stream.wait_event(ev_out[b])         # step i-2's X_A has left this buffer
-            plan.obs_prep(STRIDE, 0, None, bdX, V)
-            plan.analysis(br, V, bD, dXB=bdX, XB=bdX, XA=bXA, M=M)
-            ev_done[b].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[b])
-                h_XA[b].copy_(bXA, non_blocking=True)
-                ev_out[b].record(s_out)
-        for b in range(min(2, nsteps)):
-            stream.wait_event(ev_out[b])
-
+    # sets of device buffers; step i's inputs (deviations, background, innovations, variances) are
+    # copied in on one stream while step i-1 computes, and step i-2's X_A is copied out on another.
+    # Every step copies all of its inputs in from pinned host memory and its X_A out inside the
+    # timed region.
     e2e_ms = float("nan")
+    h2d = d2h = 0
     if not args.no_e2e:
+        h_XB = h_dX.clone().pin_memory()
+        h_XA = [torch.empty(XA.shape, dtype=XA.dtype).pin_memory() for _ in range(2)]
+        bufs = [(dX, XB, D, r, XA), (torch.empty_like(dX), torch.empty_like(XB), torch.empty_like(D),
+                                     torch.empty_like(r), torch.empty_like(XA))]
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        e2e_steps = max(2, min(args.steps, 10))
+
+        def e2e_run(nsteps):
+            ev_in = [torch.cuda.Event() for _ in range(2)]
+            ev_done = [torch.cuda.Event() for _ in range(2)]
+            ev_out = [torch.cuda.Event() for _ in range(2)]
+            start = torch.cuda.Event()
+            start.record(stream)
+            s_in.wait_event(start)
+            for i in range(nsteps):
+                b = i & 1
+                bdX, bXB, bD, br, bXA = bufs[b]
+                with torch.cuda.stream(s_in):
+                    if i >= 2:
+                        s_in.wait_event(ev_done[b])      # step i-2 no longer reads these inputs
+                    bdX.copy_(h_dX, non_blocking=True)
+                    bXB.copy_(h_XB, non_blocking=True)
+                    bD.copy_(h_D, non_blocking=True)
+                    br.copy_(h_r, non_blocking=True)
+                    ev_in[b].record(s_in)
+                stream.wait_event(ev_in[b])
+                if i >= 2:
+                    stream.wait_event(ev_out[b])         # step i-2's X_A has left this buffer
+                plan.obs_prep(STRIDE, 0, None, bdX, V)
+                plan.analysis(br, V, bD, dXB=bdX, XB=bXB, XA=bXA, Z=Z, M=M)
+                ev_done[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[b])
+                    h_XA[b].copy_(bXA, non_blocking=True)
+                    ev_out[b].record(s_out)
+            for b in range(min(2, nsteps)):
+                stream.wait_event(ev_out[b])
+
         e2e_run(2)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -355,43 +419,61 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    h2d = h_dX.numel() * 4 + h_D.numel() * 4 + h_r.numel() * 4
-    d2h = h_XA[0].numel() * 4
+        h2d = (h_dX.numel() + h_XB.numel() + h_D.numel() + h_r.numel()) * 4
+        d2h = h_XA[0].numel() * 4
+        del h_XA, h_XB, bufs
+        # the timed step's outputs again, for the comparison below
+        step()
+        barrier()
 
-    # plain FP64 comparator on the same values (fewer steps: it is FP64-ALU bound)
+    # plain FP64 comparator on the same values (fewer steps: it is FP64-ALU bound), and the
+    # errors of this path against it on every result
     fp64 = None
     if not args.no_fp64:
-        del h_XA
         dX64 = dX.double()
         D64 = D.double()
         r64 = r.double()
         V64 = torch.empty(NENS, NOBS, dtype=torch.float64, device=dev)
+        Z64 = torch.empty(NENS, NOBS, dtype=torch.float64, device=dev)
         XA64 = torch.empty_like(dX64)
         M64 = torch.empty(NENS * NENS, dtype=torch.float64, device=dev)
         plan64 = enkf.Plan(NSTATE, NOBS, NENS, enkf.ENKF_FP64, device=dev)
 
         def step64():
             plan64.obs_prep(STRIDE, 0, None, dX64, V64)
-            plan64.analysis(r64, V64, D64, dXB=dX64, XB=dX64, XA=XA64, M=M64)
+            plan64.analysis(r64, V64, D64, dXB=dX64, XB=dX64, XA=XA64, Z=Z64, M=M64)
 
         step64()
         barrier()
         k64 = max(1, min(args.steps, 3))
+        enkf.enkf_ism_profile(plan64.handle, True)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(k64):
             step64()
         f1.record(stream)
         barrier()
+        ph64 = enkf.enkf_ism_profile_read(plan64.handle)
         ms64 = f0.elapsed_time(f1) / k64
-        # accuracy of the FP32 path against the FP64 path on X_A (same inputs)
-        err_xa = float(torch.linalg.norm(XA.double() - XA64) / torch.linalg.norm(XA64))
-        err_inc = float(torch.linalg.norm((XA.double() - dX64) - (XA64 - dX64)) / torch.linalg.norm(XA64 - dX64))
-        err_m = float(torch.linalg.norm(M.double() - M64) / torch.linalg.norm(M64))
+
+        def relerr(a, b):
+            return float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))
+
+        errs = {"Z": relerr(Z, Z64), "M": relerr(M, M64), "XA": relerr(XA, XA64),
+                "increment": relerr(XA.double() - dX64, XA64 - dX64)}
+        lv64 = ph64.get("ism_solve", (float("nan"), 1))
+        lv64_ms = lv64[0] / max(lv64[1], 1)
+        f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
         fp64 = {"path": "plain FP64 level-streaming", "ms_per_step": ms64, "analyses_per_s": 1e3 / ms64,
-                "speedup_fp32_over_fp64": ms64 / (t_max / args.steps),
-                "fp32_rel_err_vs_fp64": {"XA": err_xa, "increment": err_inc, "M": err_m}}
+                "speedup_over_fp64": ms64 / (t_max / args.steps),
+                "rel_err_vs_fp64": errs, "meets_1e-5_on_every_result": all(v <= 1e-5 for v in errs.values()),
+                "solve_roofline": {"kernel": "ism_levels_kernel<double,2>", "bound": "alu",
+                                   "achieved": f_solve / (lv64_ms / 1e3) / 1e12, "peak": peaks["fp64_tflops"],
+                                   "unit": "TFLOP/s",
+                                   "frac": f_solve / (lv64_ms / 1e3) / 1e12 / peaks["fp64_tflops"],
+                                   "peak_kind": "measured (FP64 FMA microbenchmark)", "avg_launch_ms": lv64_ms}}
         plan64.close()
+        del dX64, D64, r64, V64, Z64, XA64, M64
 
     if rank != 0:
         return
@@ -399,6 +481,9 @@ def run_ours(args):
     lv_ms, lv_n = phases.get("ism_solve", (float("nan"), 0))
     lv_avg = lv_ms / max(lv_n, 1)
     src_dir = os.path.join(ROOT, "paper_1302_3876_gb300", "csrc")
+    f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
+    fp32_peak = peaks["fp32_tflops"]
+    fp32_kind = f"measured (FP32 FMA microbenchmark, {peaks['how']})"
     if args.mode == "fp32":
         lb = level_bytes(NOBS, NENS, 4)
         achieved = lb / (lv_avg / 1e3) / 1e9
@@ -406,9 +491,8 @@ def run_ours(args):
                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_stream.cu"),
-                                               "ism_levels_large_single_fp32.md")}
+                                               f"ism_levels_{args.workload}_fp32.md")}
     elif args.mode in ("bf16", "fp16", "bf16x3"):
-        f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
         pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
         achieved = pb / (lv_avg / 1e3) / 1e9
         mult = {"bf16": 3, "fp16": 1, "bf16x3": 6}[args.mode]   # tensor products per operand pair
@@ -423,46 +507,44 @@ def run_ours(args):
                                     "frac": mult * f_solve / (lv_avg / 1e3) / 1e12 / bf16_peak,
                                     "note": "mma.sync m16n8k16; fp16 and bf16 share the dense peak"},
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_panel.cu"),
-                                               f"ism_panel_large_single_{args.mode}.md")}
+                                               f"ism_panel_{args.workload}_{args.mode}.md")}
     else:
-        f_solve = 6 * NOBS * NENS ** 2 + 3 * NOBS * NENS
         achieved = f_solve / (lv_avg / 1e3) / 1e12
-        alu_peak = fp32_alu_peak_tflops()
         pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
-        roofline = {"kernel": "ism_panel_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                    "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (no measured FP32 peak)",
+        roofline = {"kernel": "ism_panel_kernel<0>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "peak_kind": fp32_kind,
                     "algorithmic_flops_per_launch": f_solve, "avg_launch_ms": lv_avg,
                     "hbm_view": {"algorithmic_bytes_per_launch": pb, "achieved_gbs": pb / (lv_avg / 1e3) / 1e9,
                                  "peak_gbs": peak, "frac": pb / (lv_avg / 1e3) / 1e9 / peak},
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_panel.cu"),
-                                               "ism_panel_large_single_fp32.md")}
+                                               f"ism_panel_{args.workload}_fp32.md")}
     total_ms = sum(v[0] for v in phases.values())
     ms_step = t_max / args.steps
+    launches = 1 + 1 + (14 if refine else 5)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nstate": NSTATE, "nobs": NOBS, "nens": NENS,
-                   "path": {"panel32": "panel form on FP32 CUDA cores, b=%d (FP64 gamma)" % args.panel_b,
-                            "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)" % args.panel_b,
-                            "bf16x3": "panel form on tensor cores, BF16 operands split in three, b=%d (FP64 gamma)"
-                                      % args.panel_b,
-                            "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)" % args.panel_b,
-                            "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}[args.mode],
-                   "refine": bool(args.refine),
-                   "l2": "inputs 1.3 GB > L2; no flush", "parallelism": f"replicas x{world}"},
+                   "path": PATH_NAME[args.mode] % args.panel_b if "%" in PATH_NAME[args.mode] else
+                   PATH_NAME[args.mode],
+                   "refine": refine,
+                   "x_b": "a buffer of its own (values equal to dX_B)",
+                   "l2": "inputs > L2 (129 MB); no flush", "parallelism": f"replicas x{world}"},
         "gflops": flops(NSTATE, NOBS, NENS) / (ms_step / 1e3) / 1e9,
         "gamma_min": inf.gamma_min, "gamma_max": inf.gamma_max,
         "roofline": roofline,
+        "measured_peaks": {"fp32_tflops": peaks["fp32_tflops"], "fp64_tflops": peaks["fp64_tflops"],
+                           "sm_mhz_during": peaks["sm_mhz"], "hbm_gbs": peak,
+                           "bf16_tflops": read_bf16_peak(), "how": peaks["how"]},
         "phases_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in phases.items()},
         "phase_share": {k: v[0] / total_ms for k, v in phases.items()} if total_ms > 0 else {},
         "e2e": None if args.no_e2e else {
             "value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-            "note": "pinned host buffers; copies in, compute and copies out of consecutive steps overlap "
-                    "on three streams (two device buffer sets)"},
-        "gpu_launches": 7 * args.steps,   # prep, solve, Gram (2), M, split of M, X_A
+            "note": "pinned host buffers; copies in (dX_B, X_B, D, r), compute and the copy out of X_A of "
+                    "consecutive steps overlap on three streams (two device buffer sets)"},
+        "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
         "comparator_fp64": fp64,
         "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
@@ -556,6 +638,113 @@ def run_panel_single(args):
     print(json.dumps({"metric": METRIC, "workload": f"panel_single Nstate={nstate} Nobs={nobs} Nens={nens}",
                       "value": 1e3 / best[0], "unit": METRIC, "best_path_at_1e-5": best[1],
                       "fp64_plain_ms": ref64, "paths": results, "data": "synthetic"}), flush=True)
+
+
+def run_lorenz_small(args):
+    """Lorenz-96 Nstate = 40, F = 8, truth spun up 1000 RK4 steps (dt 0.01) on the device, 20 members
+    = truth + N(0, 0.1^2), every 2nd variable observed with R = 0.01 I and perturbed observations;
+    the plain FP64 path (obs-space prep with centering, then the analysis).  Latency-bound: one call
+    timed alone (median of 1000, CUDA events), 10^4 calls replayed from a captured CUDA graph, and the
+    FP64 oracle on one host core (median of 1000)."""
+    os.environ["OMP_NUM_THREADS"] = "1"     # the oracle's timing is on one core
+    import numpy as np
+    import torch
+    import synth
+    from paper_1302_3876_gb300 import enkf
+    enkf.load(build_if_missing=True)
+    dev = torch.device("cuda")
+    d = synth.lorenz_small_draws()
+    nstate, nobs, nens, stride = d["nstate"], d["nobs"], d["nens"], d["obs_stride"]
+    truth = torch.from_numpy(d["truth0"].copy()).to(dev).reshape(1, nstate)
+    enkf.enkf_forecast(truth, d["F"], 0.01, 1000)                       # spin-up on the device (RK4)
+    XB = (truth + torch.from_numpy(d["ens_noise"]).to(dev)).contiguous()
+    Y = ((truth[0, ::stride] + torch.from_numpy(d["obs_noise"]).to(dev))[None, :]
+         + torch.from_numpy(d["pert"]).to(dev)).contiguous()
+    r = torch.full((nobs,), d["r"], dtype=torch.float64, device=dev)
+    dX = torch.empty_like(XB)
+    V = torch.empty(nens, nobs, dtype=torch.float64, device=dev)
+    D = torch.empty_like(V)
+    XA = torch.empty_like(XB)
+    plan = enkf.Plan(nstate, nobs, nens, enkf.ENKF_FP64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        plan.obs_prep(stride, 1, XB, dX, V, Y=Y, D=D)
+        plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA)
+
+    for _ in range(max(args.warmup, 3)):
+        call()
+    inf = plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA, info=True)
+    assert inf.status == 0
+    ref = XA.clone()
+    # (a) one call at a time
+    single = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(1000):
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        single.append(e0.elapsed_time(e1))
+    t_single = statistics.median(single)
+    # (b) 10^4 calls replayed from a CUDA graph of one call
+    plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA, info=True)           # nothing pending at capture
+    g = torch.cuda.CUDAGraph()
+    s_cap = torch.cuda.Stream()
+    s_cap.wait_stream(stream)
+    with torch.cuda.stream(s_cap):
+        with torch.cuda.graph(g, stream=s_cap):
+            call()
+    stream.wait_stream(s_cap)
+    nrep = 10000
+    for _ in range(10):
+        g.replay()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(nrep):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / nrep
+    inf = plan.analysis(r, V, D, dXB=dX, XB=XB, XA=XA, info=True)
+    assert inf.status == 0 and torch.equal(XA, ref)
+    plan.close()
+    # FP64 oracle on one host core, same values
+    import oracle
+    XBh, Yh = XB.cpu().numpy().astype(np.float64), Y.cpu().numpy().astype(np.float64)
+    rh = np.full(nobs, d["r"])
+
+    def oracle_call():
+        _, dXo = oracle.ensemble_deviations(XBh)
+        Vo = oracle.observe_deviations(dXo, nobs, stride)
+        Do = oracle.innovations(Yh, XBh, stride)
+        return oracle.analysis(rh, Vo, Do, XBh, dXo)
+
+    oracle_call()
+    t_or = []
+    for _ in range(1000):
+        t0 = time.perf_counter()
+        out = oracle_call()
+        t_or.append(time.perf_counter() - t0)
+    t_oracle = statistics.median(t_or)
+    err = float(np.linalg.norm(ref.cpu().numpy() - out["XA"]) / np.linalg.norm(out["XA"]))
+    print(json.dumps({
+        "metric": METRIC, "workload": f"lorenz_small Nstate={nstate} Nobs={nobs} Nens={nens} (plain FP64 path)",
+        "value": 1e3 / t_graph, "unit": METRIC, "dtype": "f64", "data": "synthetic",
+        "single_call": {"analyses_per_s": 1e3 / t_single, "latency_us": 1e3 * t_single,
+                        "how": "median of 1000 calls, CUDA events around obs prep + analysis, synchronised"},
+        "graph_replay": {"analyses_per_s": 1e3 / t_graph, "latency_us": 1e3 * t_graph, "calls": nrep,
+                         "how": "one call (obs prep + analysis) captured in a CUDA graph, replayed back to back"},
+        "gpu_launches_per_analysis": 6,
+        "kernels_per_analysis": ["center_observe_kernel<double>", "ism_levels_kernel<double,2>",
+                                 "gram_upper_kernel<double>", "gram_reduce_kernel", "assemble_M_kernel",
+                                 "xa_update_kernel<double>"],
+        "clocks": clk.summary(),
+        "rel_err_XA_vs_oracle": err,
+        "cpu_baseline": {"value": 1.0 / t_oracle, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": "the same analysis (prep included), median of 1000 calls"},
+    }), flush=True)
 
 
 def run_batch_local(args):
@@ -813,7 +1002,7 @@ def run_next_rows(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -825,9 +1014,11 @@ def main():
                          "(bf16), three-piece BF16 (bf16x3) or FP16 (fp16) operands, or the FP32 level-streaming "
                          "path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
-    ap.add_argument("--refine", action="store_true", help="one step of iterative refinement (panel modes)")
-    ap.add_argument("--workload", choices=["large_single", "panel_single", "batch_local", "lorenz_cycle",
-                                           "next_rows"], default="large_single")
+    ap.add_argument("--refine", action=argparse.BooleanOptionalAction, default=True,
+                    help="one step of iterative refinement (panel modes; on by default: the refined FP32 path is "
+                         "the one that meets 1e-5 on Z, M, X_A and the increment)")
+    ap.add_argument("--workload", choices=["panel_single", "large_single", "panel_paths", "lorenz_small",
+                                           "batch_local", "lorenz_cycle", "next_rows"], default="panel_single")
     ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "pivot", "cycle"], default="all",
                     help="next_rows workload: run one part only")
     ap.add_argument("--cycles", type=int, default=200, help="next_rows workload: assimilation cycles per filter")
@@ -838,8 +1029,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "panel_single":
+    elif args.workload == "panel_paths":
         run_panel_single(args)
+    elif args.workload == "lorenz_small":
+        run_lorenz_small(args)
     elif args.workload == "batch_local":
         run_batch_local(args)
     elif args.workload == "lorenz_cycle":
