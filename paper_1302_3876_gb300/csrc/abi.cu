@@ -14,7 +14,7 @@ using namespace enkf;
 
 namespace {
 
-thread_local char g_last_error[512] = "";
+thread_local char g_last_error[1024] = "";
 
 enkf_status fail(enkf_status s, const char* fmt, ...) {
     va_list ap;
@@ -48,6 +48,9 @@ struct enkf_ism_plan_s {
     uint32_t flags;
     int device;
     bool fp64;
+    bool small;          // the whole analysis in one CTA (small.cu)
+    bool tc5;            // three-piece BF16 panel solve on tcgen05 (ism_panel_tc05.cu)
+    Tc5Launch T5;
     size_t w;                 // element size
     LevelLaunch L;
     PanelLaunch P;
@@ -55,7 +58,7 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, total;
+        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, off_vpc, off_upc, total;
     int64_t ldp;              // row pitch of the 16-bit operand pieces (tensor-core panel modes)
     bool refine;
     // latched status of the previous call
@@ -140,8 +143,14 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
                                                          : 0;
             e = panel_plan(nobs, nens, p->panel_b, prec, &p->P);
             p->L.grid = p->P.grid;
+            if (e == cudaSuccess && prec == 3 && p->panel_b == tc5_panel_b()) {
+                e = tc5_plan(nobs, nens, &p->T5);
+                p->tc5 = e == cudaSuccess;
+                if (p->tc5 && p->T5.grid > p->L.grid) p->L.grid = p->T5.grid;
+            }
         } else {
             e = level_plan(p->fp64, nobs, nens, &p->L);
+            p->small = !(flags & ENKF_FLAG_TEST_TIMEOUT) && small_fits(p->fp64, nobs, nens);
         }
     }
     if (e != cudaSuccess) {
@@ -174,6 +183,8 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
         p->ldp = (nobs + 63 + 7) / 8 * 8;
         p->off_vp = o; o = align256(o + sizeof(uint16_t) * (size_t)pieces * N * p->ldp);
         p->off_up = o; o = align256(o + sizeof(uint16_t) * 2 * (size_t)pieces * panel_max_b() * p->ldp);
+        p->off_vpc = o; o = align256(o + (p->tc5 ? tc5_vpc_bytes(nobs, nens) : 0));
+        p->off_upc = o; o = align256(o + (p->tc5 ? tc5_upc_bytes(nobs) : 0));
     }
     p->refine = panel && (flags & ENKF_FLAG_REFINE);
     if (p->refine) {
@@ -343,6 +354,31 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
     a.test_skip_arrival = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 1 : 0;
     a.timeout_ns = (p->flags & ENKF_FLAG_TEST_TIMEOUT) ? 20000000ull : 2000000000ull;
     int slot = prof_begin(p, 1, s);
+    if (p->small) {
+        SmallArgs sa;
+        sa.nobs = (int32_t)p->nobs;
+        sa.nens = p->nens;
+        sa.nstate = p->nstate;
+        sa.r = r;
+        sa.V = V;
+        sa.ldv = ldv;
+        sa.D = D;
+        sa.ldd = ldd;
+        sa.dXB = dXB;
+        sa.ldx = ldx;
+        sa.XB = XB;
+        sa.ldb = ldb;
+        sa.XA = XA;
+        sa.lda = lda;
+        sa.Z = Z;
+        sa.ldz = ldz;
+        sa.M = M;
+        sa.gamma = a.gamma;
+        sa.ctl = ctl;
+        sa.check = a.check;
+        CU(small_launch(p->fp64, sa, s), "small-problem launch");
+        prof_end(p, slot, s);
+    } else {
     PanelArgs panel_args;
     if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16 ||
         p->mode == ENKF_PANEL_BF16X3) {
@@ -376,7 +412,13 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.vp = (unsigned short*)(ws + p->off_vp);
         pa.up = (unsigned short*)(ws + p->off_up);
         pa.ldp = p->ldp;
-        CU(panel_launch(p->P, pa, s), "panel launch");
+        cudaError_t et = cudaErrorNotSupported;
+        if (p->tc5) {
+            et = tc5_solve(p->T5, pa, ws + p->off_vpc, ws + p->off_upc, s);
+            if (et == cudaErrorNotSupported) (void)cudaGetLastError();
+            else CU(et, "tensor-core panel launch");
+        }
+        if (et == cudaErrorNotSupported) CU(panel_launch(p->P, pa, s), "panel launch");
         panel_args = pa;
     } else {
         CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
@@ -455,6 +497,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             prof_end(p, slot, s);
         }
     }
+    }   // not the small-problem path
     CU(cudaMemcpyAsync(p->h_status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status copy");
     CU(cudaEventRecord(p->done, s), "cudaEventRecord");
     p->pending = true;
@@ -489,9 +532,29 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                            cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) return cuda_fail(e, "refine residual norm copy");
         }
+        {
+            Control hc;
+            cudaMemcpy(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+            if (st == 0 && hc.pad[42] != 0)
+                return fail(ENKF_ERR_CUDA, "shared-memory guard bands corrupted: %x, first bad word %08x at %d",
+                            hc.pad[42], hc.pad[43], hc.pad[44]);
+        }
         if (st != 0) {
             Control hc;
             cudaMemcpy(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+            if (hc.pad[0] != 0) {
+                char msg[900];
+                snprintf(msg, sizeof(msg),
+                         "device status %s (level %d; wait site %d, CTA %d, tile %d, parity %d, thread %d, phase %d; "
+                         "expired waits per site 1-15: %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d; progress %d %d %d "
+                         "%d; as_full %08x %08x as_empty %08x %08x d2_full %08x %08x; waited %08x %08x; guards %x %08x at %d)",
+                         enkf_status_string((enkf_status)st), hc.fail_level, hc.pad[0], hc.pad[1], hc.pad[2], hc.pad[3],
+                         hc.pad[4], hc.pad[5], hc.pad[11], hc.pad[12], hc.pad[13], hc.pad[14], hc.pad[15], hc.pad[16],
+                         hc.pad[17], hc.pad[18], hc.pad[19], hc.pad[20], hc.pad[21], hc.pad[22], hc.pad[23], hc.pad[24],
+                         hc.pad[25], hc.pad[30], hc.pad[31], hc.pad[32], hc.pad[33], hc.pad[34], hc.pad[35], hc.pad[36],
+                         hc.pad[37], hc.pad[38], hc.pad[39], hc.pad[40], hc.pad[41], hc.pad[42], hc.pad[43], hc.pad[44]);
+                return fail((enkf_status)st, "%s", msg);
+            }
             return fail((enkf_status)st, "device status %s (level %d)", enkf_status_string((enkf_status)st),
                         hc.fail_level);
         }

@@ -34,6 +34,26 @@ struct LevelArgs {
     uint64_t timeout_ns;
 };
 
+// Whole analysis of a small problem in one CTA (small.cu): V, U and Z resident in shared
+// memory.  XB/dXB/XA, Z and M are optional (NULL).
+struct SmallArgs {
+    int32_t nobs, nens;
+    int64_t nstate;
+    const void* r;
+    const void* V; int64_t ldv;
+    const void* D; int64_t ldd;
+    const void* dXB; int64_t ldx;
+    const void* XB; int64_t ldb;
+    void* XA; int64_t lda;
+    void* Z; int64_t ldz;
+    void* M;
+    double* gamma;                 // [nens]
+    Control* ctl;
+    int32_t check;
+};
+bool small_fits(bool fp64, int64_t nobs, int32_t nens);
+cudaError_t small_launch(bool fp64, const SmallArgs& a, cudaStream_t s);
+
 struct LevelLaunch {
     int grid;
     int threads;
@@ -89,6 +109,22 @@ int panel_max_b();
 int panel_pieces(int prec);   // 16-bit operand pieces of the tensor-core variants (0: FP32 cores)
 cudaError_t panel_plan(int64_t nobs, int32_t nens, int32_t b, int32_t prec, PanelLaunch* out);
 cudaError_t panel_launch(const PanelLaunch& L, PanelArgs a, cudaStream_t s);
+
+// Panel solve with the trailing update and the dots on tcgen05 tensor cores (three BF16
+// pieces per value, b = 32 levels per panel; ism_panel_tc05.cu), preceded by a Step-1
+// pass.  Workspace: tc5_vpc_bytes (V pieces) and tc5_upc_bytes (two panels' U_P pieces).
+struct Tc5Launch {
+    int grid, ntiles, tiles_per_blk;
+    size_t smem;
+    int64_t part_stride;
+};
+size_t tc5_vpc_bytes(int64_t nobs, int32_t nens);
+size_t tc5_upc_bytes(int64_t nobs);
+int tc5_panel_b();
+cudaError_t tc5_plan(int64_t nobs, int32_t nens, Tc5Launch* out);
+// Uses p.r, V, D, U, Z (and lds), part, coefg, C, gamma, ctl, check, timeout_ns.
+// cudaErrorNotSupported when U or Z is not TMA-aligned.
+cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, cudaStream_t s);
 
 // Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,
 // partials in double; then Q = sum of the partials in a fixed order.
