@@ -154,14 +154,28 @@ __device__ bool reduce_coefs(const LevelArgs& a, const Smem& s, int first_u, uns
     const int N = a.nens, NN = 2 * N;
     const unsigned nblk = gridDim.x;
     const int tid = threadIdx.x;
+    if (nblk == 1) {
+        // one CTA: its own sums are the totals (a block barrier orders the global accesses)
+        __syncthreads();
+        for (int i = tid; i < NN; i += blockDim.x) s.coef[i] = s.acc[i];
+        __syncthreads();
+        return ld_volatile_s32(&a.ctl->status) == 0;
+    }
     for (int i = tid; i < NN; i += blockDim.x) __stcg(&a.part[(int64_t)blockIdx.x * NN + i], s.acc[i]);
     if (!grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, s.flag)) return false;
-    for (int idx = blockIdx.x; idx < NN; idx += nblk) {
-        if (idx >= N && idx < N + first_u) continue;
-        double v = 0.0;
-        for (int b = tid; b < (int)nblk; b += blockDim.x) v += __ldcg(&a.part[(int64_t)b * NN + idx]);
-        v = block_sum(v, s.red);
-        if (tid == 0) __stcg(&a.coefg[idx], v);
+    // one warp per entry: lane l sums CTAs l, l + 32, ... in order, then a fixed butterfly.
+    // (A block-wide FP64 reduction per entry costs microseconds on GB300's narrow FP64 pipe.)
+    {
+        const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+        int j = 0;
+        for (int idx = blockIdx.x; idx < NN; idx += nblk, ++j) {
+            if (idx >= N && idx < N + first_u) continue;
+            if (j % nw != warp) continue;
+            double v = 0.0;
+            for (int b = lane; b < (int)nblk; b += 32) v += __ldcg(&a.part[(int64_t)b * NN + idx]);
+            v = warp_sum(v);
+            if (lane == 0) __stcg(&a.coefg[idx], v);
+        }
     }
     if (!grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, s.flag)) return false;
     for (int i = tid; i < NN; i += blockDim.x) s.coef[i] = __ldcg(&a.coefg[i]);
@@ -247,11 +261,13 @@ __global__ void __launch_bounds__(kThreads) ism_levels_kernel(LevelArgs a) {
             }
         }
         const bool last = (k + 1 == N);
-        const T ginv = (T)(1.0 / gam);
+        // one FP64 division per level, by one thread (GB300's FP64 pipe is narrow)
+        if (tid == 0) s.red[0] = 1.0 / gam;
         for (int i = tid; i < NN; i += blockDim.x) s.acc[i] = 0.0;
         for (int64_t c0 = 0; c0 < nrows; c0 += RC) {
             const int n = (int)((nrows - c0) < (int64_t)RC ? (nrows - c0) : (int64_t)RC);
             __syncthreads();
+            const T ginv = (T)s.red[0];
             const T* uk = U + (int64_t)k * a.ldu + r0 + c0;
             const T* vn = V + (int64_t)(k + 1) * a.ldv + r0 + c0;
             for (int j = tid; j < n; j += blockDim.x) {

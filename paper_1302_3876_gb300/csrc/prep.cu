@@ -20,11 +20,15 @@ __global__ void center_observe_kernel(int64_t nstate, int64_t nobs, int n, int s
                                       double scale) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nstate;
          i += (int64_t)gridDim.x * blockDim.x) {
+        // unrolled so that several member loads are in flight (a small problem is bound by
+        // their latency); the sum runs in member order
         double s = 0.0;
+#pragma unroll 8
         for (int e = 0; e < n; ++e) s += (double)XB[(int64_t)e * ldb + i];
         const double mean = s / (double)n;
         const bool observed = (i % stride == 0) && (i / stride < nobs);
         const int64_t j = i / stride;
+#pragma unroll 8
         for (int e = 0; e < n; ++e) {
             const T x = XB[(int64_t)e * ldb + i];
             const T d = (T)((double)x - mean);
