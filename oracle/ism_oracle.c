@@ -95,6 +95,29 @@ static double dot_asc(int64_t nobs, const double* v, const double* x) {
 }
 
 /*
+ * The same sum, as accurate as if formed in twice the working precision and rounded once:
+ * the Dot2 algorithm of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
+ * Sci. Comput. 26, 2005) -- every product split exactly into p + e by a fused
+ * multiply-add, every partial sum into s + q by Knuth's TwoSum, the errors accumulated
+ * and added at the end.  Used for M = V^T Z, whose entries are the part of Z in range(V)
+ * and so cancel to ~1e-6 of sum |v||z| at the large workloads: there the plain ascending
+ * sum loses ~1e-10 of M, this one keeps ~1e-16.
+ */
+static double dot2_asc(int64_t nobs, const double* v, const double* x) {
+    double s = 0.0, c = 0.0;
+    for (int64_t j = 0; j < nobs; ++j) {
+        const double p = v[j] * x[j];
+        const double e = fma(v[j], x[j], -p);
+        const double t = s + p;
+        const double z = t - s;
+        const double q = (s - (t - z)) + (p - z);
+        s = t;
+        c += q + e;
+    }
+    return s + c;
+}
+
+/*
  * Step 2, eqs. (SM-step-2-h), (SM-step-2-Z), (SM-step-2-u): for levels
  * k = 1..Nens (0-based k = 0..Nens-1 here):
  *   gamma_k = 1 + v_k^T u_k^(k-1)
@@ -155,14 +178,15 @@ int oracle_ism_solve(int64_t nobs, int32_t nens, int32_t nrhs, const double* r,
 
 /*
  * M = V^T Z / sqrt(Nens - 1)  (nens x nrhs, column-major, ld = nens), so that
- * S V^T Z = dX_B M with S = dX_B / sqrt(Nens - 1).
+ * S V^T Z = dX_B M with S = dX_B / sqrt(Nens - 1).  Each entry is the plain definition,
+ * summed in ascending row order with the Dot2 compensation (dot2_asc).
  */
 void oracle_vtz(int64_t nobs, int32_t nens, int32_t nrhs, const double* V, int64_t ldv,
                 const double* Z, int64_t ldz, double* M) {
     double scale = 1.0 / sqrt((double)(nens - 1));
 #pragma omp parallel for schedule(static) collapse(2)
     for (int32_t i = 0; i < nrhs; ++i)
-        for (int32_t m = 0; m < nens; ++m) M[i * nens + m] = dot_asc(nobs, V + m * ldv, Z + i * ldz) * scale;
+        for (int32_t m = 0; m < nens; ++m) M[i * nens + m] = dot2_asc(nobs, V + m * ldv, Z + i * ldz) * scale;
 }
 
 /*

@@ -11,12 +11,12 @@ from P = V^T Z1 (fixed-point digits on the tensor cores), T = D - r o Z1 (FP32 F
 product V P (three BF16 pieces); enkf_ism_info.refine_resid reports its norm relative to
 ||R^-1 D||.  The oracle forms the same quantity in FP64 from the same Z1 (the unrefined
 solve of the same plan parameters is deterministic).  The device residual is a small
-difference of two FP32-rounded terms: T = D - r o Z1 and V P both carry ~1e-7 of their own
-size, which is ~1e-3 of the residual here, so the two norms are held to agree to 1e-2.
-That is the precision the refinement needs (its contraction is set by the stored
-factors, not by the residual); what needs more is P, whose error would reach M through
-the cancellation in V^T Z, and the refined Z and M are checked against the oracle in
-test_gpu_mixed.py.
+difference of large terms: the rounding of P (~2^-32 of sum |v||z|) times V is comparable
+to a residual of ~4e-5 at gamma ~ 5000, so the two norms are held to 25% (they agree to
+~0.3% at gamma ~ 300).  That rounding does not reach the refined result: the same P
+enters the residual and M = P + V^T delta, so it cancels to first order.  What the
+refinement must achieve is checked on the exact residual: the oracle's FP64 residual of
+the refined Z is at most half that of Z1.
 """
 import numpy as np
 import pytest
@@ -83,9 +83,12 @@ def test_refinement_residual_matches_oracle(mode, nobs, nens):
     res = oracle.residual(r, V, D, Z1) / r[None, :]
     want = np.linalg.norm(res) / np.linalg.norm(D / r[None, :])
     got = inf.refine_resid
-    print(f"mode {mode} nobs={nobs} nens={nens}: scaled residual device {got:.6e}, oracle {want:.6e}")
+    after = np.linalg.norm(oracle.residual(r, V, D, Zr) / r[None, :]) / np.linalg.norm(D / r[None, :])
+    print(f"mode {mode} nobs={nobs} nens={nens}: scaled residual device {got:.6e}, oracle {want:.6e}; "
+          f"after the refinement {after:.6e}")
     assert want > 0.0
-    assert got == pytest.approx(want, rel=1e-2)
+    assert got == pytest.approx(want, rel=0.25)
+    assert after <= 0.5 * want
     # and the refined Z is closer to the oracle's solution than Z1
     Z = oracle.ism_solve(r, V, D)
     assert rel(Zr, Z) <= rel(Z1, Z)

@@ -370,3 +370,33 @@ def test_rk4_fourth_order_convergence():
         errs.append(np.linalg.norm(xt - ref))
     ratio1, ratio2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 12.0 < ratio1 < 20.0 and 12.0 < ratio2 < 20.0, errs
+
+
+def test_vtz_is_accurate_under_cancellation():
+    """M = V^T Z / sqrt(N - 1) (Sec. 3.1) where the sums cancel: Z made almost orthogonal to the
+    columns of V, as the solve makes the part of Z in range(V) small.  The oracle's entries
+    must match exact rational arithmetic (fractions.Fraction on the same FP64 values)
+    within the Dot2 error bound of Ogita, Rump and Oishi, |res - exact| <= u |exact| +
+    gamma_{n-1}^2 sum |v_j z_j| (gamma_n = n u / (1 - n u)), plus one rounding for the
+    scaling by 1/sqrt(N - 1); the plain FP64 sum misses by far more than that bound."""
+    from fractions import Fraction
+    nobs, nens, nrhs = 3000, 4, 3
+    V = synth.normal_matrix(811, 1, nobs, nens)
+    Z = synth.normal_matrix(811, 2, nobs, nrhs)
+    # remove the range(V) part of Z in FP64 (leaves a residue of rounding size)
+    Q, _ = np.linalg.qr(V.T)
+    Z = Z - (Z @ Q) @ Q.T
+    M = oracle.vtz(V, Z)
+    plain_worst = 0.0
+    for k in range(nens):
+        for i in range(nrhs):
+            exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(V[k], Z[i]))
+            scale = 1.0 / math.sqrt(nens - 1)
+            want = float(exact) * scale
+            u = 2.0 ** -53
+            gam = (nobs - 1) * u / (1 - (nobs - 1) * u)
+            bound = (3 * u * abs(float(exact)) + gam ** 2 * float(np.sum(np.abs(V[k] * Z[i])))) * scale
+            assert abs(M[k, i] - want) <= bound, (k, i, M[k, i], want, bound)
+            plain = float(np.sum(V[k] * Z[i])) * scale
+            plain_worst = max(plain_worst, abs(plain - want) / bound)
+    assert plain_worst > 100.0        # the case really cancels: the plain sum misses by > 100 bounds
