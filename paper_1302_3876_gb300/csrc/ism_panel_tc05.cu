@@ -21,7 +21,7 @@
 //   - X: four epilogue warps, one per 32-row quarter of the tile, each with a ring of
 //     four slots of 32 rows x 32 columns FP32 (TMA, 128-byte swizzle); a warp refills a
 //     slot with the next tile's block as soon as it is done with it.
-//   - U_P and V_{P'} pieces: 24 KB per tile each, laid out in global memory in the
+//   - U_P pieces (two buffers) and V_{P'} pieces (one): 24 KB per tile each, laid out in global memory in the
 //     canonical K-major order of the MMA operands (written once per panel by the
 //     previous sweep, or by the Step-1 pass for V) and brought in by one bulk copy.
 //   - K (and beta) pieces: computed per chunk (per sweep) by the whole CTA.
@@ -74,9 +74,9 @@ constexpr int kOffMisc = 0;
 constexpr int kMiscBytes = 1024;
 constexpr int kOffSlots = 2048;                                // 16 x 4 KB (1024-aligned for the swizzle)
 constexpr int kOffAs = kOffSlots + NQ * NS * kSlotBytes + kGuard;   // 2 x 24 KB   MMA2 A slices
-constexpr int kOffVp = kOffAs + 2 * kOp3 + kGuard;                  // 2 x 24 KB   V_{P'} pieces
-constexpr int kOffUp = kOffVp + 2 * kOp3 + kGuard;                  // 24 KB       U_P pieces
-constexpr int kOffKp = kOffUp + kOp3 + kGuard;                      // 24 KB       K pieces
+constexpr int kOffVp = kOffAs + 2 * kOp3 + kGuard;                  // 24 KB       V_{P'} pieces
+constexpr int kOffUp = kOffVp + kOp3 + kGuard;                      // 2 x 24 KB   U_P pieces
+constexpr int kOffKp = kOffUp + 2 * kOp3 + kGuard;                  // 24 KB       K pieces
 constexpr int kOffBp = kOffKp + kOp3 + kGuard;                      // 6 KB        beta pieces
 constexpr int kOffW = kOffBp + kBeta3 + kGuard;                     // 4 KB        W (float)
 constexpr int kEnd = kOffW + PB * PB * 4 + kGuard;
@@ -95,7 +95,7 @@ static_assert(kSmem <= 232448, "shared memory of one CTA");
 
 struct Tc5Shared {
     uint64_t slot_full[NQ * NS];
-    uint64_t up_full, up_empty, vp_full[2], vp_empty[2];
+    uint64_t up_full[2], up_empty[2], vp_full, vp_empty;
     uint64_t d1_full[2], d1_empty[2], d2_full[2], d2_empty[2], d3_full, d3_empty;
     // one pair per epilogue warp (one waiter and one signaller each, so that parity waits stay
     // in step); the two A-slice buffers are shared by warps q and q + 2
@@ -514,37 +514,44 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 for (int s = s0; s < s1; ++s) mbar_drain(&sh->slot_full[q * NS + s], c.gt & 1, a.timeout_ns);
             }
         } else if (warp == kMmaWarp) {
-            // ---------------- one thread issues every MMA: per step i, MMA1 of tile i, MMA2 of tile i - 1
-            // (whose A slices the epilogue finishes while MMA1(i) runs), then MMA3 of tile i
+            // ---------------- one thread issues every MMA.  Per step i: MMA1 of tile i, MMA2 of tile
+            // i - 1 (whose A slices the epilogue finishes while MMA1(i) runs), MMA3 of tile i.  The
+            // U_P pieces are double-buffered (tile i + 1 is loaded while tile i is used), the V
+            // pieces single-buffered (V(i) is loaded at the end of step i, once MMA2(i - 1) is done,
+            // a step before MMA2(i) needs it).
             if (lane == 0 && (upd || dots)) {
                 Counters c = cn;
                 const unsigned id1 = instr_desc(TR, CW), id3 = instr_desc(TR, PB), id2 = instr_desc(TR, PB);
                 const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+                auto load_up = [&](unsigned g, int tile) {
+                    mbar_expect_tx(&sh->up_full[g & 1], kOp3);
+                    bulk_load(up + (g & 1) * kOp3, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0 + tile),
+                              kOp3, &sh->up_full[g & 1]);
+                };
+                auto load_vp = [&](int tile) {
+                    mbar_expect_tx(&sh->vp_full, kOp3);
+                    bulk_load(vp, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + tile), kOp3, &sh->vp_full);
+                };
                 if (upd) {
-                    mbar_expect_tx(&sh->up_full, kOp3);
-                    bulk_load(up, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0), kOp3, &sh->up_full);
+                    load_up(c.g1, 0);
+                    if (ntl >= 2) load_up(c.g1 + 1, 1);
                 }
-                if (dots)
-                    for (int j = 0; j < 2 && j < ntl; ++j) {
-                        const unsigned b = (c.g2 + j) & 1;
-                        mbar_expect_tx(&sh->vp_full[b], kOp3);
-                        bulk_load(vp + b * kOp3, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + j), kOp3,
-                                  &sh->vp_full[b]);
-                    }
+                if (dots) load_vp(0);
                 for (int it = 0; ok && it <= ntl; ++it) {
                     if (upd && it < ntl) {
-                        if (!waitx(&sh->up_full, c.g1 & 1, 6, it, sh, a) ||
+                        if (!waitx(&sh->up_full[c.g1 & 1], (c.g1 >> 1) & 1, 6, it, sh, a) ||
                             (c.g1 >= 2 && !waitx(&sh->d1_empty[c.g1 & 1], ((c.g1 >> 1) - 1) & 1, 13, it, sh, a))) {
                             ok = false;
                             break;
                         }
                         fence_after();
                         const unsigned d1 = tbase + kD1 + (c.g1 & 1) * CW;
+                        const unsigned char* ub = up + (c.g1 & 1) * kOp3;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
                             for (int q = 0; q < 6; ++q)
-                                mma_bf16(d1, smem_desc(up + pa[q] * kPiece + ks * (TR * 32)),
+                                mma_bf16(d1, smem_desc(ub + pa[q] * kPiece + ks * (TR * 32)),
                                          smem_desc(kp + pb[q] * kPiece + ks * (CW * 32)), id1, (ks | q) != 0);
                         mma_commit(&sh->d1_full[c.g1 & 1]);
                     }
@@ -552,7 +559,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         // MMA2 of tile it - 1
                         const int jt = it - 1;
                         const unsigned b = c.g2 & 1;
-                        if (!waitx(&sh->vp_full[b], (c.g2 >> 1) & 1, 9, jt, sh, a) ||
+                        if (!waitx(&sh->vp_full, c.g2 & 1, 9, jt, sh, a) ||
                             (c.g2 >= 2 && !waitx(&sh->d2_empty[b], ((c.g2 >> 1) - 1) & 1, 14, jt, sh, a))) {
                             ok = false;
                             break;
@@ -566,7 +573,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                             }
                             fence_after();
                             const unsigned char* asb = as + (sig & 1) * kOp3;
-                            const unsigned char* vb = vp + b * kOp3 + q * (PB * 32 * 2);
+                            const unsigned char* vb = vp + q * (PB * 32 * 2);
 #pragma unroll
                             for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
@@ -578,21 +585,13 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         }
                         if (!ok) break;
                         mma_commit(&sh->d2_full[b]);
-                        mma_commit(&sh->vp_empty[b]);
-                        if (jt + 2 < ntl) {
-                            if (!waitx(&sh->vp_empty[b], (c.g2 >> 1) & 1, 11, jt, sh, a)) {
-                                ok = false;
-                                break;
-                            }
-                            mbar_expect_tx(&sh->vp_full[b], kOp3);
-                            bulk_load(vp + b * kOp3, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + jt + 2), kOp3,
-                                      &sh->vp_full[b]);
-                        }
+                        mma_commit(&sh->vp_empty);
                         c.g2++;
                     }
                     if (upd && it < ntl) {
                         // MMA3 after MMA2 of the previous tile: its D3 buffer is free once the epilogue
                         // has finished that tile, which needs those MMA2 slices
+                        const unsigned char* ub = up + (c.g1 & 1) * kOp3;
                         if (mat) {
                             if (c.g3 >= 1 && !waitx(&sh->d3_empty, (c.g3 - 1) & 1, 7, it, sh, a)) {
                                 ok = false;
@@ -603,38 +602,43 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                             for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
                                 for (int q = 0; q < 6; ++q)
-                                    mma_bf16(tbase + kD3, smem_desc(up + pa[q] * kPiece + ks * (TR * 32)),
+                                    mma_bf16(tbase + kD3, smem_desc(ub + pa[q] * kPiece + ks * (TR * 32)),
                                              smem_desc(bpc + pb[q] * (PB * PB * 2) + ks * (PB * 32)), id3,
                                              (ks | q) != 0);
                             mma_commit(&sh->d3_full);
                         }
-                        mma_commit(&sh->up_empty);
-                        if (it + 1 < ntl) {
-                            // the next tile's U_P pieces once MMA1 and MMA3 of this one have read the buffer
-                            if (!waitx(&sh->up_empty, c.g1 & 1, 8, it, sh, a)) {
+                        mma_commit(&sh->up_empty[c.g1 & 1]);
+                        // the buffer of tile it - 1 takes tile it + 1 once its MMAs have read it
+                        if (it >= 1 && it + 1 < ntl) {
+                            const unsigned gp = c.g1 - 1;
+                            if (!waitx(&sh->up_empty[gp & 1], (gp >> 1) & 1, 8, it, sh, a)) {
                                 ok = false;
                                 break;
                             }
-                            mbar_expect_tx(&sh->up_full, kOp3);
-                            bulk_load(up, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0 + it + 1), kOp3,
-                                      &sh->up_full);
+                            load_up(gp, it + 1);
                         }
                         c.g1++;
                         if (mat) c.g3++;
                     }
-                }
-                // wait for the completions not waited for above (the last U_P buffer release and the
-                // last two V buffer releases of the chunk), so that every later parity wait on these
-                // barriers is for the phase right after the last one observed
-                if (ok && upd && ntl > 0 && !waitx(&sh->up_empty, (c.g1 - 1) & 1, 8, ntl, sh, a)) ok = false;
-                if (ok && dots)
-                    for (int jt = (ntl >= 2 ? ntl - 2 : 0); jt < ntl; ++jt) {
-                        const unsigned g = c.g2 - (unsigned)(ntl - jt);
-                        if (!waitx(&sh->vp_empty[g & 1], (g >> 1) & 1, 11, jt, sh, a)) {
+                    // V(it) once MMA2(it - 1) has read the buffer: a step before MMA2(it) needs it
+                    if (ok && dots && it >= 1 && it < ntl) {
+                        if (!waitx(&sh->vp_empty, (c.g2 - 1) & 1, 11, it, sh, a)) {
                             ok = false;
                             break;
                         }
+                        load_vp(it);
                     }
+                }
+                // wait for the buffer releases not waited for above (the last two U_P tiles, the last
+                // V tile), so that every later parity wait on these barriers is for the phase right
+                // after the last one observed
+                if (ok && upd)
+                    for (int jt = (ntl >= 2 ? ntl - 2 : 0); ok && jt < ntl; ++jt) {
+                        const unsigned g = c.g1 - (unsigned)(ntl - jt);
+                        if (!waitx(&sh->up_empty[g & 1], (g >> 1) & 1, 8, jt, sh, a)) ok = false;
+                    }
+                // (the release by MMA2 of the chunk's last tile)
+                if (ok && dots && ntl > 0 && !waitx(&sh->vp_empty, (c.g2 - 1) & 1, 11, ntl, sh, a)) ok = false;
                 // the commit arrives once every MMA issued above has completed
                 mma_commit(&sh->drained_a);
                 mbar_drain(&sh->drained_a, sh->flag[0] & 1, a.timeout_ns);
@@ -684,10 +688,10 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         for (int q = 0; q < NQ * NS; ++q) mbar_init(&sh->slot_full[q], 1);
-        mbar_init(&sh->up_full, 1);
-        mbar_init(&sh->up_empty, 1);
+        mbar_init(&sh->vp_full, 1);
+        mbar_init(&sh->vp_empty, 1);
         for (int q = 0; q < 2; ++q) {
-            mbar_init(&sh->vp_full[q], 1), mbar_init(&sh->vp_empty[q], 1);
+            mbar_init(&sh->up_full[q], 1), mbar_init(&sh->up_empty[q], 1);
             mbar_init(&sh->d1_full[q], 1), mbar_init(&sh->d1_empty[q], NEPI * 32);
             mbar_init(&sh->d2_full[q], 1), mbar_init(&sh->d2_empty[q], NEPI * 32);
         }
@@ -803,66 +807,88 @@ struct Step1Args {
 __global__ void __launch_bounds__(256) tc5_step1_kernel(Step1Args a) {
     const int N = a.nens;
     const int npan = (N + PB - 1) / PB;
-    // items: (tile, column, 8-row group) for the V columns (pieces and U) and the D columns (Z),
-    // then (tile, row, 8-wide t group) for panel 0's U_P pieces
-    const int64_t nv = (int64_t)a.ntiles * npan * PB * 16;
-    const int64_t nd = (int64_t)a.ntiles * N * 16;
-    const int64_t nu = (int64_t)a.ntiles * TR * 4;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv + nd + nu;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        if (q < nv + nd) {
-            const bool isv = q < nv;
-            const int64_t e = isv ? q : q - nv;
-            const int rg = (int)(e % 16);
-            const int64_t rest = e / 16;
-            const int col = isv ? (int)(rest % (npan * PB)) : (int)(rest % N);
-            const int64_t T = isv ? rest / (npan * PB) : rest / N;
-            const int64_t row0 = T * TR + rg * 8;
-            float v8[8];
+    const int64_t T = blockIdx.x;                        // one 128-row tile per CTA
+    const int tid = threadIdx.x;
+    const int rg = tid & 15, cl = tid >> 4;              // 8-row group, column lane (16 per pass)
+    const int64_t row0 = T * TR + rg * 8;
+    // 1 / r of this thread's 8 rows (rows past nobs: 0, so that every product below is 0)
+    float rinv[8];
+    bool bad = false;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int64_t row = row0 + j;
-                float x = 0.f;
-                if (row < a.nobs && col < N) {
-                    x = isv ? a.V[(int64_t)col * a.ldv + row] : a.D[(int64_t)col * a.ldd + row];
-                    const float rj = a.r[row];
-                    if (a.check && !(rj > 0.f && isfinite(rj) && isfinite(x))) {
-                        set_status(a.ctl, kErrNumeric);
-                        a.ctl->fail_level = 0;
-                    }
-                    const float s = x * (1.0f / rj);
-                    if (isv) a.U[(int64_t)col * a.ldu + row] = s;
-                    else a.Z[(int64_t)col * a.ldz + row] = s;
-                }
-                v8[j] = x;
-            }
-            if (isv) {
-                const int pv = col / PB, t = col % PB;
-                unsigned char* dst = a.vpc + ((int64_t)pv * a.ntiles + T) * (int64_t)kOp3 + (rg >> 2) * (PB * 32 * 2) +
-                                     ((rg & 3) >> 1) * (PB * 32) + (t >> 3) * 256 + (rg & 1) * 128 + (t & 7) * 16;
-                uint4 pc[3];
-                pieces8(v8, pc);
-#pragma unroll
-                for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dst + pq * kPiece) = pc[pq];
-            }
-        } else {
-            const int64_t e = q - nv - nd;
-            const int t8 = (int)(e % 4);
-            const int m = (int)((e / 4) % TR);
-            const int64_t T = e / (4 * TR);
-            const int64_t row = T * TR + m;
-            float v8[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int t = t8 * 8 + j;
-                v8[j] = (row < a.nobs && t < N) ? a.V[(int64_t)t * a.ldv + row] * (1.0f / a.r[row]) : 0.f;
-            }
-            uint4 pc[3];
-            pieces8(v8, pc);
-            unsigned char* dst = a.upc + T * (int64_t)kOp3 + kmaj_off(m, t8, TR * 32);
-#pragma unroll
-            for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dst + pq * kPiece) = pc[pq];
+    for (int j = 0; j < 8; ++j) {
+        const int64_t row = row0 + j;
+        rinv[j] = 0.f;
+        if (row < a.nobs) {
+            const float rj = a.r[row];
+            if (!(rj > 0.f && isfinite(rj))) bad = true;
+            rinv[j] = 1.0f / rj;
         }
+    }
+    const bool full = row0 + 8 <= a.nobs;
+    // V columns: U = V / r, the V pieces of every panel; D columns: Z = D / r
+    for (int c = cl; c < npan * PB + N; c += 16) {
+        const bool isv = c < npan * PB;
+        const int col = isv ? c : c - npan * PB;
+        float x8[8];
+        const float* src = isv ? a.V + (int64_t)col * a.ldv : a.D + (int64_t)col * a.ldd;
+        const bool have = col < N;
+        const bool vec = have && full && (((uintptr_t)(src + row0)) & 15) == 0;
+        if (vec) {
+            const float4 p0 = *reinterpret_cast<const float4*>(src + row0);
+            const float4 p1 = *reinterpret_cast<const float4*>(src + row0 + 4);
+            x8[0] = p0.x, x8[1] = p0.y, x8[2] = p0.z, x8[3] = p0.w, x8[4] = p1.x, x8[5] = p1.y, x8[6] = p1.z,
+            x8[7] = p1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x8[j] = (have && row0 + j < a.nobs) ? src[row0 + j] : 0.f;
+        }
+        float s8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (!isfinite(x8[j])) bad = true;
+            s8[j] = x8[j] * rinv[j];
+        }
+        if (have) {
+            float* dst = isv ? a.U + (int64_t)col * a.ldu : a.Z + (int64_t)col * a.ldz;
+            if (full && (((uintptr_t)(dst + row0)) & 15) == 0) {
+                *reinterpret_cast<float4*>(dst + row0) = make_float4(s8[0], s8[1], s8[2], s8[3]);
+                *reinterpret_cast<float4*>(dst + row0 + 4) = make_float4(s8[4], s8[5], s8[6], s8[7]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (row0 + j < a.nobs) dst[row0 + j] = s8[j];
+            }
+        }
+        if (isv) {
+            const int pv = col / PB, t = col % PB;
+            unsigned char* dstp = a.vpc + ((int64_t)pv * a.ntiles + T) * (int64_t)kOp3 + (rg >> 2) * (PB * 32 * 2) +
+                                  ((rg & 3) >> 1) * (PB * 32) + (t >> 3) * 256 + (rg & 1) * 128 + (t & 7) * 16;
+            uint4 pc[3];
+            pieces8(x8, pc);
+#pragma unroll
+            for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dstp + pq * kPiece) = pc[pq];
+        }
+    }
+    // panel 0's U_P pieces: thread (row m, 8-wide group t8), U = V / r of the first 32 columns
+    for (int e = tid; e < TR * 4; e += 256) {
+        const int t8 = e & 3, m = e >> 2;
+        const int64_t row = T * TR + m;
+        float v8[8];
+        const float ri = row < a.nobs ? 1.0f / a.r[row] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int t = t8 * 8 + j;
+            v8[j] = (row < a.nobs && t < N) ? a.V[(int64_t)t * a.ldv + row] * ri : 0.f;
+        }
+        uint4 pc[3];
+        pieces8(v8, pc);
+        unsigned char* dst = a.upc + T * (int64_t)kOp3 + kmaj_off(m, t8, TR * 32);
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dst + pq * kPiece) = pc[pq];
+    }
+    if (a.check && bad) {
+        set_status(a.ctl, kErrNumeric);
+        a.ctl->fail_level = 0;
     }
 }
 
@@ -927,7 +953,7 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
     s1.upc = static_cast<unsigned char*>(upc);
     s1.ctl = p.ctl;
     s1.check = p.check;
-    tc5_step1_kernel<<<152 * 8, 256, 0, s>>>(s1);
+    tc5_step1_kernel<<<L.ntiles, 256, 0, s>>>(s1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     Tc5Args a;
