@@ -99,9 +99,11 @@ static double dot_asc(int64_t nobs, const double* v, const double* x) {
  * the Dot2 algorithm of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
  * Sci. Comput. 26, 2005) -- every product split exactly into p + e by a fused
  * multiply-add, every partial sum into s + q by Knuth's TwoSum, the errors accumulated
- * and added at the end.  Used for M = V^T Z, whose entries are the part of Z in range(V)
- * and so cancel to ~1e-6 of sum |v||z| at the large workloads: there the plain ascending
- * sum loses ~1e-10 of M, this one keeps ~1e-16.
+ * and added at the end.  Used for V^T Z, whose entries are the part of Z in range(V) and
+ * so cancel to ~1e-6 of sum |v||z| at the large workloads: the plain ascending sum would
+ * lose ~1e-10 of them, this one keeps ~1e-16 of the sum as given.  (The rounding error of
+ * an FP64 solve's Z is a larger effect on M at such gamma; ism_solve_refined in the Python
+ * module removes it by one step of refinement.)
  */
 static double dot2_asc(int64_t nobs, const double* v, const double* x) {
     double s = 0.0, c = 0.0;
@@ -208,7 +210,8 @@ void oracle_analysis_update(int64_t nstate, int32_t nens, int32_t nrhs, const do
 /*
  * Residual of the analysis linear system, eq. (EnKSM:system-to-solve-V):
  *   Res = D - (R + V V^T) Z = D - (r o Z + V (V^T Z)).
- * P = V^T Z is formed first (nens x nrhs), then each entry of Res.
+ * P = V^T Z is formed first (nens x nrhs, each entry by dot2_asc: its entries cancel, and
+ * an error in P enters Res undamped), then each entry of Res.
  */
 int oracle_residual(int64_t nobs, int32_t nens, int32_t nrhs, const double* r, const double* V, int64_t ldv,
                     const double* D, int64_t ldd, const double* Z, int64_t ldz, double* Res, int64_t ldr) {
@@ -216,7 +219,7 @@ int oracle_residual(int64_t nobs, int32_t nens, int32_t nrhs, const double* r, c
     if (!P) return -1;
 #pragma omp parallel for schedule(static) collapse(2)
     for (int32_t i = 0; i < nrhs; ++i)
-        for (int32_t m = 0; m < nens; ++m) P[i * nens + m] = dot_asc(nobs, V + m * ldv, Z + i * ldz);
+        for (int32_t m = 0; m < nens; ++m) P[i * nens + m] = dot2_asc(nobs, V + m * ldv, Z + i * ldz);
 #pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < nrhs; ++i) {
         for (int64_t j = 0; j < nobs; ++j) {

@@ -51,7 +51,7 @@ def check_problem(base, out, d):
     r = base[d["r"]:d["r"] + n].astype(np.float64)
     V = base[d["V"]:d["V"] + n * N].astype(np.float64).reshape(N, n)
     D = base[d["D"]:d["D"] + n * N].astype(np.float64).reshape(N, n)
-    Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
+    Z, gamma = oracle.ism_solve_refined(r, V, D, return_gamma=True)
     M = oracle.vtz(V, Z)
     Zd = out[d["Z"]:d["Z"] + n * N].astype(np.float64).reshape(N, n)
     Md = out[d["M"]:d["M"] + N * N].astype(np.float64).reshape(N, N).T

@@ -73,7 +73,7 @@ def reference(r, V, D, dXB):
     key = (V.shape, float(r[0]), float(D[0, 0]), float(V[-1, -1]))
     if key in _REF:
         return _REF[key]
-    Z, gamma = oracle.ism_solve(r, V, D, return_gamma=True)
+    Z, gamma = oracle.ism_solve_refined(r, V, D, return_gamma=True)
     M = oracle.vtz(V, Z)
     out = (Z, gamma, M, oracle.analysis_update(dXB, dXB, M))
     if V.shape[1] >= 200000:   # keep the latest full-size reference only

@@ -80,7 +80,7 @@ def run_device(mode, r, V, D, dXB=None, XB=None, ld_pad=0, info=True, flags=0, a
 def oracle_of(mode, r, V, D, dXB=None, XB=None):
     dt = NP[mode]
     r64, V64, D64 = rounded(r, dt), rounded(V, dt), rounded(D, dt)
-    Z, gamma = oracle.ism_solve(r64, V64, D64, return_gamma=True)
+    Z, gamma = oracle.ism_solve_refined(r64, V64, D64, return_gamma=True)
     out = {"Z": Z, "gamma": gamma}
     if V.shape[0] >= 2:
         out["M"] = oracle.vtz(V64, Z)
@@ -323,7 +323,7 @@ def test_large_single_full_size(mode):
     assert rel(host(tV), V_o) <= TOL[mode]
     r64 = host(tr)
     D64 = host(tD)
-    Z, gamma = oracle.ism_solve(r64, V_o, D64, return_gamma=True)
+    Z, gamma = oracle.ism_solve_refined(r64, V_o, D64, return_gamma=True)
     assert rel(host(tZ), Z) <= TOL[mode]
     M = oracle.vtz(V_o, Z)
     XA = oracle.analysis_update(dX64, dX64, M)

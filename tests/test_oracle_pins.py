@@ -400,3 +400,45 @@ def test_vtz_is_accurate_under_cancellation():
             plain = float(np.sum(V[k] * Z[i])) * scale
             plain_worst = max(plain_worst, abs(plain - want) / bound)
     assert plain_worst > 100.0        # the case really cancels: the plain sum misses by > 100 bounds
+
+
+def test_refined_solve_gives_the_m_of_the_exact_solution():
+    """M = V^T Z / sqrt(N - 1) with Z the solution of (R + V V^T) Z = D (Sec. 3.1), at gamma ~ 1e6.
+    Exact rational arithmetic on the same FP64 inputs gives V^T Z = (I + V^T R^-1 V)^-1 V^T R^-1 D
+    (the ensemble-space form of the Woodbury identity, eq. SWM).  Any Z stored in FP64 carries
+    a rounding of ~u |Z| that the damping of range(V) does not shrink, so V^T Z can be no
+    closer than ~u gamma_max: the refined oracle must be within that bound, and the plain
+    solve (one pass of Step 2, whose rounding accumulates over the levels) is not."""
+    from fractions import Fraction
+
+    def exact_vtz(r, V, D):
+        nens, nobs = V.shape
+        rf = [Fraction(float(x)) for x in r]
+        Vf = [[Fraction(float(x)) for x in row] for row in V]
+        Df = [[Fraction(float(x)) for x in row] for row in D]
+        A = [[(1 if k == m else 0) + sum(Vf[k][j] * Vf[m][j] / rf[j] for j in range(nobs)) for m in range(nens)]
+             for k in range(nens)]
+        B = [[sum(Vf[k][j] * Df[i][j] / rf[j] for j in range(nobs)) for i in range(D.shape[0])] for k in range(nens)]
+        for c in range(nens):                       # Gauss-Jordan, exact (A is SPD: no pivoting needed)
+            for rr in range(nens):
+                if rr != c:
+                    f = A[rr][c] / A[c][c]
+                    A[rr] = [a - f * b for a, b in zip(A[rr], A[c])]
+                    B[rr] = [a - f * b for a, b in zip(B[rr], B[c])]
+        return np.array([[float(B[k][i] / A[k][k]) for i in range(D.shape[0])] for k in range(nens)])
+
+    u = 2.0 ** -53
+    for seed in (1, 2, 3):
+        nobs, nens, nrhs = 300, 4, 3
+        V = 58.0 * synth.normal_matrix(900 + seed, 1, nobs, nens)
+        D = synth.normal_matrix(900 + seed, 2, nobs, nrhs)
+        r = synth.uniform(900 + seed, 3, nobs, 0.5, 1.5)
+        want = exact_vtz(r, V, D) / math.sqrt(nens - 1)
+        err = lambda M: np.linalg.norm(M - want) / np.linalg.norm(want)
+        Zr, gamma = oracle.ism_solve_refined(r, V, D, return_gamma=True)
+        bound = u * gamma.max()
+        assert 5e5 < gamma.min() and gamma.max() < 5e6, gamma
+        assert err(oracle.vtz(V, Zr)) <= bound, (seed, err(oracle.vtz(V, Zr)), bound)
+        assert err(oracle.vtz(V, oracle.ism_solve(r, V, D))) > bound     # the plain solve misses it
+        ref = oracle.analysis(r, V, D, np.zeros((nens, 5)), np.zeros((nens, 5)))
+        assert np.array_equal(ref["M"], oracle.vtz(V, Zr))
