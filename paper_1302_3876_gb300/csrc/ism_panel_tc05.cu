@@ -224,11 +224,40 @@ __device__ void check_guards(const unsigned char* sm, Control* ctl) {
     }
 }
 
+// Phase timers (built only with -DENKF_TC5_TIMERS, for profiling): SM-clock cycles summed
+// per CTA in the unused bytes between the first guard band and the X slots, then into a
+// device array read by enkf_tc5_timers_read.  Entries 0..15: time in the waits of each
+// site (lane 0 of the waiting warp); 16..: phases timed by thread 0 and the MMA thread.
+constexpr int kOffTimers = kMiscBytes + kGuard;
+constexpr int kNTimers = (kOffSlots - kOffTimers) / 8;
+enum { kTmK = 16, kTmEpi = 17, kTmEnd = 18, kTmRed = 19, kTmFac = 20, kTmAll = 21, kTmChunks = 22, kTmMma = 23,
+       kTmStep1 = 24 };
+#ifdef ENKF_TC5_TIMERS
+__device__ unsigned long long g_tc5_timers[kNTimers];
+__device__ __forceinline__ unsigned long long* tc5_tacc(const void* sm) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<uintptr_t>(sm) + kOffTimers);
+}
+#define TC5_T0(v) const long long v = clock64()
+#define TC5_ADD(smb, i, t0) atomicAdd(tc5_tacc(smb) + (i), (unsigned long long)(clock64() - (t0)))
+#define TC5_CNT(smb, i) atomicAdd(tc5_tacc(smb) + (i), 1ull)
+#else
+#define TC5_T0(v)
+#define TC5_ADD(smb, i, t0)
+#define TC5_CNT(smb, i)
+#endif
+
 // Bounded wait that, when it gives up first, records where (site id, CTA, tile, parity,
 // thread) in the control block's diagnostic words, so that the host can report it.
 __device__ __forceinline__ bool waitx(uint64_t* bar, unsigned parity, int site, int tile, Tc5Shared* sh,
                                       const Tc5Args& a) {
+#ifdef ENKF_TC5_TIMERS
+    TC5_T0(tw);
+    const bool okw = mbar_wait(bar, parity, &sh->err, a.ctl, a.timeout_ns);
+    if ((threadIdx.x & 31) == 0 && site < 16) TC5_ADD(sh, site, tw);
+    if (okw) return true;
+#else
     if (mbar_wait(bar, parity, &sh->err, a.ctl, a.timeout_ns)) return true;
+#endif
     if (atomicCAS(&a.ctl->pad[0], 0, site) == 0) {
         a.ctl->pad[1] = blockIdx.x;
         a.ctl->pad[2] = tile;
@@ -284,6 +313,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
         const int64_t ldx = zpart ? a.ldz : a.ldu;
         const bool mat = sp.mat && ch == 0 && upd;
         const bool writeup = ch == 0 && !zpart && upd && nbn > 0;      // next panel's U_P pieces
+        TC5_T0(tk);
         __syncthreads();
         if (tid == 0) sh->flag[3] = 1000 * sp.k0 + 100 * (sp.bp > 0) + 10 * (sp.nb > 0) + ch;
         // ---- K = -W A for this chunk's columns (and beta once per sweep), as BF16 pieces
@@ -331,6 +361,10 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
         }
         fence_async_smem();
         __syncthreads();
+#ifdef ENKF_TC5_TIMERS
+        if (tid == 0) TC5_ADD(sm, kTmK, tk), TC5_CNT(sm, kTmChunks);
+#endif
+        TC5_T0(te);
         bool ok = true;
         if (warp < NEPI) {
             // ---------------- epilogue warp (q, h): rows 32 q .. 32 q + 31 of every tile, columns
@@ -374,24 +408,17 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                     break;
                 }
                 fence_after();
-                // the slice buffer is free once MMA2 has read slice sig - 2 (warp q + 2 of the previous
-                // tile, or warp q - 2 of this one), whose commit arrives on this warp's as_empty: its
-                // k-th completion is the one this warp waits for at its k-th wait
-                if (dots && sig >= 2) {
-                    const unsigned k = q < 2 ? c.g2 - 1 : c.g2;
-                    if (!waitx(&sh->as_empty[q], k & 1, 12, it, sh, a)) {
-                        ok = false;
-                        break;
-                    }
-                }
+                // (1) X_new = X + D1 for both slots: written back to the slot (for the transposed
+                // reads below) and stored; the next panel's U_P pieces from chunk 0
                 for (int s = s0; s < s1; ++s) {
                     unsigned char* slot = myslots + s * kSlotBytes;
                     if (!waitx(&sh->slot_full[q * NS + s], c.gt & 1, 4, it, sh, a)) {
                         ok = false;
                         break;
                     }
+                    if (!upd) continue;
                     float d[SWC];
-                    if (upd) {
+                    {
                         unsigned u0[16], u1[16];
                         tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC, u0);
                         tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC + 16, u1);
@@ -404,10 +431,10 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
 #pragma unroll
                     for (int j = 0; j < SWC; ++j) {
                         float* p = slot_at(slot, j, lane);
-                        xn[j] = upd ? *p + d[j] : *p;
-                        if (upd) *p = xn[j];
+                        xn[j] = *p + d[j];
+                        *p = xn[j];
                     }
-                    if (upd && row < a.nobs) {
+                    if (row < a.nobs) {
 #pragma unroll
                         for (int j = 0; j < SWC; ++j)
                             if (s * SWC + j < ncl) X[(int64_t)(acol0 + s * SWC + j) * ldx + row] = xn[j];
@@ -428,10 +455,30 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                                 *reinterpret_cast<uint4*>(ub + pq * kPiece + kmaj_off(m, t8, TR * 32)) = pc[pq];
                         }
                     }
+                }
+                if (!ok) break;
+                if (upd) {
+                    // D1 has been read: MMA1 of tile it + 2 may overwrite it
+                    fence_before();
+                    mbar_arrive(&sh->d1_empty[c.g1 & 1]);
+                }
+                // (2) the slice buffer is free once MMA2 has read slice sig - 2 (warp q + 2 of the
+                // previous tile, or warp q - 2 of this one), whose commit arrives on this warp's
+                // as_empty: its k-th completion is the one this warp waits for at its k-th wait
+                if (dots && sig >= 2) {
+                    const unsigned k = q < 2 ? c.g2 - 1 : c.g2;
+                    if (!waitx(&sh->as_empty[q], k & 1, 12, it, sh, a)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                // (3) the slots' 32 columns x this quarter's 32 rows -> pieces of MMA2's A operand
+                // (M = chunk column, K = row): lane = column, four 8-row groups; then the slot
+                // takes the next tile's block
+                for (int s = s0; s < s1; ++s) {
+                    unsigned char* slot = myslots + s * kSlotBytes;
                     if (dots) {
                         __syncwarp();
-                        // the slot's 32 columns x this quarter's 32 rows -> pieces of MMA2's A operand
-                        // (M = chunk column, K = row): lane = column, four 8-row groups
                         const int cm = s * SWC + lane;
 #pragma unroll
                         for (int g4 = 0; g4 < 4; ++g4) {
@@ -457,11 +504,6 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         mbar_expect_tx(&sh->slot_full[q * NS + s], kSlotBytes);
                         tma_load_2d(slot, tm, (T + 1) * TR + q * 32, acol0 + s * SWC, &sh->slot_full[q * NS + s]);
                     }
-                }
-                if (!ok) break;
-                if (upd) {
-                    fence_before();
-                    mbar_arrive(&sh->d1_empty[c.g1 & 1]);
                 }
                 if (dots) mbar_arrive(&sh->as_full[q]);
                 if (lane == 0) ((volatile int*)sh->prog)[warp] = 16 * (int)c.gt + 2;
@@ -520,6 +562,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
             // pieces single-buffered (V(i) is loaded at the end of step i, once MMA2(i - 1) is done,
             // a step before MMA2(i) needs it).
             if (lane == 0 && (upd || dots)) {
+                TC5_T0(tm);
                 Counters c = cn;
                 const unsigned id1 = instr_desc(TR, CW), id3 = instr_desc(TR, PB), id2 = instr_desc(TR, PB);
                 const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
@@ -643,14 +686,22 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 mma_commit(&sh->drained_a);
                 mbar_drain(&sh->drained_a, sh->flag[0] & 1, a.timeout_ns);
                 sh->flag[0]++;
+                TC5_ADD(sm, kTmMma, tm);
             }
             __syncwarp();
         }
+#ifdef ENKF_TC5_TIMERS
+        if (tid == 0) TC5_ADD(sm, kTmEpi, te);
+#endif
+        TC5_T0(tn);
         // the generic-proxy stores of this chunk (X, the next U_P pieces, the final panel
         // columns) are read by TMA and bulk copies (async proxy) in later sweeps
         asm volatile("fence.proxy.async;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) check_guards(sm, a.ctl);
+#ifdef ENKF_TC5_TIMERS
+        if (tid == 0) TC5_ADD(sm, kTmEnd, tn);
+#endif
         if (sh->err) return false;
         // every role advanced the counters by the same tiles
         cn.gt += ntl;
@@ -666,6 +717,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
 // order, then a fixed butterfly.
 __device__ bool reduce_tc5(const Tc5Args& a, Tc5Shared* sh, int nvals, unsigned& epoch) {
     const unsigned nblk = gridDim.x;
+    TC5_T0(tr);
     if (!grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, &sh->flag[2])) return false;
     const int per = (nvals + (int)nblk - 1) / (int)nblk;
     const int e0 = blockIdx.x * per, e1 = min(e0 + per, nvals);
@@ -676,7 +728,11 @@ __device__ bool reduce_tc5(const Tc5Args& a, Tc5Shared* sh, int nvals, unsigned&
         v = warp_sum(v);
         if (lane == 0) __stcg(&a.coefg[e], v);
     }
-    return grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, &sh->flag[2]);
+    const bool okb = grid_barrier(a.ctl, nblk, epoch, a.timeout_ns, &sh->flag[2]);
+#ifdef ENKF_TC5_TIMERS
+    if (threadIdx.x == 0) TC5_ADD(sh, kTmRed, tr);
+#endif
+    return okb;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __grid_constant__ CUtensorMap tmU,
@@ -704,6 +760,10 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
         for (int q = 0; q < 4; ++q) sh->flag[q] = 0;
         mbar_init_fence();
     }
+#ifdef ENKF_TC5_TIMERS
+    TC5_T0(tall);
+    for (int i = tid; i < kNTimers; i += kThreads) tc5_tacc(sm)[i] = 0ull;
+#endif
     for (int g = 0; g < kNGuard; ++g)
         for (int i = tid; i < kGuard / 4; i += kThreads) reinterpret_cast<unsigned*>(sm + guard_off(g))[i] = kGuardWord;
     if (warp == kAllocWarp) tmem_alloc(&sh->taddr, kTmemCols);
@@ -734,6 +794,7 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
         const int bp = (N - k0) < b ? (N - k0) : b;
         const int k1 = k0 + bp;
         const int ncols_prev = (N - k0) + N;
+        TC5_T0(tf);
         // factor of the panel (every CTA): the FP64 Gram split into float hi + lo
         for (int e = tid; e < PB * PB; e += kThreads) {
             const int t = e / PB, u = e % PB;
@@ -765,6 +826,9 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
             }
             if (lane < bp) a.C[(int64_t)(k0 + lane) * N + i] = (double)v;
         }
+#ifdef ENKF_TC5_TIMERS
+        if (tid == 0) TC5_ADD(sm, kTmFac, tf);
+#endif
         nb = (N - k1) < b ? (N - k1) : b;
         SweepSpec s2 = {k0, bp, k1, k1, nb, bp, ncols_prev, 1, (k0 / b) & 1};
         ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, s2, cn);
@@ -773,6 +837,11 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
     }
     fence_before();
     __syncthreads();
+#ifdef ENKF_TC5_TIMERS
+    if (tid == 0) TC5_ADD(sm, kTmAll, tall);
+    __syncthreads();
+    for (int i = tid; i < kNTimers; i += kThreads) atomicAdd(&g_tc5_timers[i], tc5_tacc(sm)[i]);
+#endif
     if (warp == kAllocWarp) {
         fence_after();
         tmem_dealloc(tbase, kTmemCols);
@@ -985,3 +1054,18 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
 }
 
 }  // namespace enkf
+
+#ifdef ENKF_TC5_TIMERS
+// Profiling build only: copies the summed phase timers (SM cycles over all CTAs) to host
+// and optionally clears them.
+extern "C" __attribute__((visibility("default"))) int enkf_tc5_timers_read(unsigned long long* out, int n,
+                                                                          int reset) {
+    if (n > enkf::kNTimers) n = enkf::kNTimers;
+    if (cudaMemcpyFromSymbol(out, enkf::g_tc5_timers, sizeof(unsigned long long) * n) != cudaSuccess) return -1;
+    if (reset) {
+        static const unsigned long long zero[enkf::kNTimers] = {};
+        if (cudaMemcpyToSymbol(enkf::g_tc5_timers, zero, sizeof(zero)) != cudaSuccess) return -1;
+    }
+    return n;
+}
+#endif
