@@ -151,8 +151,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-__device__ __forceinline__ unsigned short bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16(x)); }
-__device__ __forceinline__ float bf16_val(unsigned short h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
 
 // The three BF16 pieces of 8 values as three 16-byte rows (each the rounding of what the
 // previous pieces leave; the subtractions are exact in FP32).
@@ -228,11 +226,11 @@ __device__ void check_guards(const unsigned char* sm, Control* ctl) {
 // per CTA in the unused bytes between the first guard band and the X slots, then into a
 // device array read by enkf_tc5_timers_read.  Entries 0..15: time in the waits of each
 // site (lane 0 of the waiting warp); 16..: phases timed by thread 0 and the MMA thread.
-constexpr int kOffTimers = kMiscBytes + kGuard;
-constexpr int kNTimers = (kOffSlots - kOffTimers) / 8;
 enum { kTmK = 16, kTmEpi = 17, kTmEnd = 18, kTmRed = 19, kTmFac = 20, kTmAll = 21, kTmChunks = 22, kTmMma = 23,
        kTmStep1 = 24 };
 #ifdef ENKF_TC5_TIMERS
+constexpr int kOffTimers = kMiscBytes + kGuard;
+constexpr int kNTimers = (kOffSlots - kOffTimers) / 8;
 __device__ unsigned long long g_tc5_timers[kNTimers];
 __device__ __forceinline__ unsigned long long* tc5_tacc(const void* sm) {
     return reinterpret_cast<unsigned long long*>(reinterpret_cast<uintptr_t>(sm) + kOffTimers);
@@ -309,8 +307,6 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
         const int gidx = zpart ? nU + cc0 : cc0;                         // first trailing column
         const int acol0 = zpart ? cc0 : sp.k1 + cc0;                      // first column in its array
         const CUtensorMap* tm = zpart ? tmZ : tmU;
-        float* X = zpart ? a.Z : a.U;
-        const int64_t ldx = zpart ? a.ldz : a.ldu;
         const bool mat = sp.mat && ch == 0 && upd;
         const bool writeup = ch == 0 && !zpart && upd && nbn > 0;      // next panel's U_P pieces
         TC5_T0(tk);
@@ -434,10 +430,13 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         xn[j] = *p + d[j];
                         *p = xn[j];
                     }
-                    if (row < a.nobs) {
-#pragma unroll
-                        for (int j = 0; j < SWC; ++j)
-                            if (s * SWC + j < ncl) X[(int64_t)(acol0 + s * SWC + j) * ldx + row] = xn[j];
+                    // X_new to global memory from the slot by TMA (rows past nobs and columns past
+                    // N lie outside the tensor and are not written)
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(tm, T * TR + q * 32, acol0 + s * SWC, slot);
+                        bulk_commit();
                     }
                     if (writeup && s == 0) {
                         // pieces of the next panel's U_P (trailing columns 0 .. nbn-1) for this row
@@ -501,6 +500,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0 && it + 1 < ntl) {
+                        if (upd) bulk_wait_read0();       // the slot's store has read it
                         mbar_expect_tx(&sh->slot_full[q * NS + s], kSlotBytes);
                         tma_load_2d(slot, tm, (T + 1) * TR + q * 32, acol0 + s * SWC, &sh->slot_full[q * NS + s]);
                     }
@@ -551,6 +551,8 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                                    (double)acc2[t]);
                 }
             }
+            // this chunk's X stores complete (their writes are read by TMA in later sweeps)
+            if (lane == 0 && upd) bulk_wait0();
             if (!ok && lane == 0) {
                 // copies still in flight land before the CTA may leave
                 for (int s = s0; s < s1; ++s) mbar_drain(&sh->slot_full[q * NS + s], c.gt & 1, a.timeout_ns);
