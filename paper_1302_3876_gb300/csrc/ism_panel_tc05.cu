@@ -73,10 +73,12 @@ constexpr int kGuard = 256;
 constexpr int kOffMisc = 0;
 constexpr int kMiscBytes = 1024;
 constexpr int kOffSlots = 2048;                                // 16 x 4 KB (1024-aligned for the swizzle)
-constexpr int kOffAs = kOffSlots + NQ * NS * kSlotBytes + kGuard;   // 2 x 24 KB   MMA2 A slices
-constexpr int kOffVp = kOffAs + 2 * kOp3 + kGuard;                  // 24 KB       V_{P'} pieces
-constexpr int kOffUp = kOffVp + kOp3 + kGuard;                      // 2 x 24 KB   U_P pieces
-constexpr int kOffKp = kOffUp + 2 * kOp3 + kGuard;                  // 24 KB       K pieces
+constexpr int kNAs = 3;                                             // A-slice buffers
+static_assert(kNAs == 3 && NQ == 4, "the A-slice buffer rotation below assumes 3 buffers, 4 quarters");
+constexpr int kOffAs = kOffSlots + NQ * NS * kSlotBytes + kGuard;   // 3 x 24 KB   MMA2 A slices
+constexpr int kOffVp = kOffAs + kNAs * kOp3 + kGuard;               // 24 KB       V_{P'} pieces
+constexpr int kOffUp = kOffVp + kOp3 + kGuard;                      // 24 KB       U_P pieces
+constexpr int kOffKp = kOffUp + kOp3 + kGuard;                      // 24 KB       K pieces
 constexpr int kOffBp = kOffKp + kOp3 + kGuard;                      // 6 KB        beta pieces
 constexpr int kOffW = kOffBp + kBeta3 + kGuard;                     // 4 KB        W (float)
 constexpr int kEnd = kOffW + PB * PB * 4 + kGuard;
@@ -397,7 +399,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 const int T = T0 + it;
                 const int64_t row = (int64_t)T * TR + q * 32 + lane;
                 const unsigned sig = 4u * c.g2 + (unsigned)q;          // this warp's MMA2 slice
-                unsigned char* asb = as + (sig & 1) * kOp3;
+                unsigned char* asb = as + (sig % kNAs) * kOp3;
                 if (lane == 0) ((volatile int*)sh->prog)[warp] = 16 * (int)c.gt + 1;
                 if (upd && !waitx(&sh->d1_full[c.g1 & 1], (c.g1 >> 1) & 1, 3, it, sh, a)) {
                     ok = false;
@@ -461,11 +463,12 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                     fence_before();
                     mbar_arrive(&sh->d1_empty[c.g1 & 1]);
                 }
-                // (2) the slice buffer is free once MMA2 has read slice sig - 2 (warp q + 2 of the
-                // previous tile, or warp q - 2 of this one), whose commit arrives on this warp's
-                // as_empty: its k-th completion is the one this warp waits for at its k-th wait
-                if (dots && sig >= 2) {
-                    const unsigned k = q < 2 ? c.g2 - 1 : c.g2;
+                // (2) slice sig goes to buffer sig % 3, free once MMA2 has read slice sig - 3 (row
+                // quarter q + 1 of the previous tile, or quarter 0 of this one for q = 3), whose
+                // commit arrives on this warp's as_empty.  MMA2 takes the slices in order, so that
+                // completion cannot be overtaken by the next one before this warp has waited for it.
+                if (dots && sig >= kNAs) {
+                    const unsigned k = q == NQ - 1 ? c.g2 : c.g2 - 1;
                     if (!waitx(&sh->as_empty[q], k & 1, 12, it, sh, a)) {
                         ok = false;
                         break;
@@ -558,137 +561,122 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 for (int s = s0; s < s1; ++s) mbar_drain(&sh->slot_full[q * NS + s], c.gt & 1, a.timeout_ns);
             }
         } else if (warp == kMmaWarp) {
-            // ---------------- one thread issues every MMA.  Per step i: MMA1 of tile i, MMA2 of tile
-            // i - 1 (whose A slices the epilogue finishes while MMA1(i) runs), MMA3 of tile i.  The
-            // U_P pieces are double-buffered (tile i + 1 is loaded while tile i is used), the V
-            // pieces single-buffered (V(i) is loaded at the end of step i, once MMA2(i - 1) is done,
-            // a step before MMA2(i) needs it).
-            if (lane == 0 && (upd || dots)) {
+            // ---------------- MMA1 and MMA3, one thread.  Step i: MMA1 of tile i (once its U_P pieces
+            // have landed and the epilogue has released the D1 buffer of tile i - 2), then MMA3 of tile
+            // i; U_P(i + 1) is loaded once those have read the (single) buffer, which is more than a
+            // tile before MMA1(i + 1) can start (the epilogue still holds D1 of tile i - 1).
+            if (lane == 0 && upd) {
                 TC5_T0(tm);
                 Counters c = cn;
-                const unsigned id1 = instr_desc(TR, CW), id3 = instr_desc(TR, PB), id2 = instr_desc(TR, PB);
+                const unsigned id1 = instr_desc(TR, CW), id3 = instr_desc(TR, PB);
                 const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
-                auto load_up = [&](unsigned g, int tile) {
-                    mbar_expect_tx(&sh->up_full[g & 1], kOp3);
-                    bulk_load(up + (g & 1) * kOp3, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0 + tile),
-                              kOp3, &sh->up_full[g & 1]);
+                auto load_up = [&](int tile) {
+                    mbar_expect_tx(&sh->up_full[0], kOp3);
+                    bulk_load(up, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0 + tile), kOp3, &sh->up_full[0]);
                 };
-                auto load_vp = [&](int tile) {
-                    mbar_expect_tx(&sh->vp_full, kOp3);
-                    bulk_load(vp, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + tile), kOp3, &sh->vp_full);
-                };
-                if (upd) {
-                    load_up(c.g1, 0);
-                    if (ntl >= 2) load_up(c.g1 + 1, 1);
-                }
-                if (dots) load_vp(0);
-                for (int it = 0; ok && it <= ntl; ++it) {
-                    if (upd && it < ntl) {
-                        if (!waitx(&sh->up_full[c.g1 & 1], (c.g1 >> 1) & 1, 6, it, sh, a) ||
-                            (c.g1 >= 2 && !waitx(&sh->d1_empty[c.g1 & 1], ((c.g1 >> 1) - 1) & 1, 13, it, sh, a))) {
+                load_up(0);
+                for (int it = 0; ok && it < ntl; ++it) {
+                    if (!waitx(&sh->up_full[0], c.g1 & 1, 6, it, sh, a) ||
+                        (c.g1 >= 2 && !waitx(&sh->d1_empty[c.g1 & 1], ((c.g1 >> 1) - 1) & 1, 13, it, sh, a))) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const unsigned d1 = tbase + kD1 + (c.g1 & 1) * CW;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                        for (int q = 0; q < 6; ++q)
+                            mma_bf16(d1, smem_desc(up + pa[q] * kPiece + ks * (TR * 32)),
+                                     smem_desc(kp + pb[q] * kPiece + ks * (CW * 32)), id1, (ks | q) != 0);
+                    mma_commit(&sh->d1_full[c.g1 & 1]);
+                    if (mat) {
+                        // D3 is free once the epilogue has written tile i - 1's final columns
+                        if (c.g3 >= 1 && !waitx(&sh->d3_empty, (c.g3 - 1) & 1, 7, it, sh, a)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        const unsigned d1 = tbase + kD1 + (c.g1 & 1) * CW;
-                        const unsigned char* ub = up + (c.g1 & 1) * kOp3;
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
                             for (int q = 0; q < 6; ++q)
-                                mma_bf16(d1, smem_desc(ub + pa[q] * kPiece + ks * (TR * 32)),
-                                         smem_desc(kp + pb[q] * kPiece + ks * (CW * 32)), id1, (ks | q) != 0);
-                        mma_commit(&sh->d1_full[c.g1 & 1]);
+                                mma_bf16(tbase + kD3, smem_desc(up + pa[q] * kPiece + ks * (TR * 32)),
+                                         smem_desc(bpc + pb[q] * (PB * PB * 2) + ks * (PB * 32)), id3,
+                                         (ks | q) != 0);
+                        mma_commit(&sh->d3_full);
                     }
-                    if (dots && it >= 1) {
-                        // MMA2 of tile it - 1
-                        const int jt = it - 1;
-                        const unsigned b = c.g2 & 1;
-                        if (!waitx(&sh->vp_full, c.g2 & 1, 9, jt, sh, a) ||
-                            (c.g2 >= 2 && !waitx(&sh->d2_empty[b], ((c.g2 >> 1) - 1) & 1, 14, jt, sh, a))) {
-                            ok = false;
-                            break;
-                        }
-                        const unsigned d2 = tbase + kD2 + b * PB;
-                        for (int q = 0; q < NQ; ++q) {
-                            const unsigned sig = 4u * c.g2 + (unsigned)q;
-                            if (!waitx(&sh->as_full[q], c.g2 & 1, 10, jt, sh, a)) {
-                                ok = false;
-                                break;
-                            }
-                            fence_after();
-                            const unsigned char* asb = as + (sig & 1) * kOp3;
-                            const unsigned char* vb = vp + q * (PB * 32 * 2);
-#pragma unroll
-                            for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-                                for (int pq = 0; pq < 6; ++pq)
-                                    mma_bf16(d2, smem_desc(asb + pa[pq] * kPiece + ks * (CW * 32)),
-                                             smem_desc(vb + pb[pq] * kPiece + ks * (PB * 32)), id2,
-                                             (q | ks | pq) != 0);
-                            mma_commit(&sh->as_empty[(q + 2) % NQ]);   // the next user of this buffer
-                        }
-                        if (!ok) break;
-                        mma_commit(&sh->d2_full[b]);
-                        mma_commit(&sh->vp_empty);
-                        c.g2++;
+                    mma_commit(&sh->up_empty[0]);
+                    // U_P(it + 1) once MMA1 and MMA3 of tile it have read the buffer (every tile's
+                    // release is waited for, so the parity waits stay in step)
+                    if (!waitx(&sh->up_empty[0], c.g1 & 1, 8, it, sh, a)) {
+                        ok = false;
+                        break;
                     }
-                    if (upd && it < ntl) {
-                        // MMA3 after MMA2 of the previous tile: its D3 buffer is free once the epilogue
-                        // has finished that tile, which needs those MMA2 slices
-                        const unsigned char* ub = up + (c.g1 & 1) * kOp3;
-                        if (mat) {
-                            if (c.g3 >= 1 && !waitx(&sh->d3_empty, (c.g3 - 1) & 1, 7, it, sh, a)) {
-                                ok = false;
-                                break;
-                            }
-                            fence_after();
-#pragma unroll
-                            for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-                                for (int q = 0; q < 6; ++q)
-                                    mma_bf16(tbase + kD3, smem_desc(ub + pa[q] * kPiece + ks * (TR * 32)),
-                                             smem_desc(bpc + pb[q] * (PB * PB * 2) + ks * (PB * 32)), id3,
-                                             (ks | q) != 0);
-                            mma_commit(&sh->d3_full);
-                        }
-                        mma_commit(&sh->up_empty[c.g1 & 1]);
-                        // the buffer of tile it - 1 takes tile it + 1 once its MMAs have read it
-                        if (it >= 1 && it + 1 < ntl) {
-                            const unsigned gp = c.g1 - 1;
-                            if (!waitx(&sh->up_empty[gp & 1], (gp >> 1) & 1, 8, it, sh, a)) {
-                                ok = false;
-                                break;
-                            }
-                            load_up(gp, it + 1);
-                        }
-                        c.g1++;
-                        if (mat) c.g3++;
-                    }
-                    // V(it) once MMA2(it - 1) has read the buffer: a step before MMA2(it) needs it
-                    if (ok && dots && it >= 1 && it < ntl) {
-                        if (!waitx(&sh->vp_empty, (c.g2 - 1) & 1, 11, it, sh, a)) {
-                            ok = false;
-                            break;
-                        }
-                        load_vp(it);
-                    }
+                    if (it + 1 < ntl) load_up(it + 1);
+                    c.g1++;
+                    if (mat) c.g3++;
                 }
-                // wait for the buffer releases not waited for above (the last two U_P tiles, the last
-                // V tile), so that every later parity wait on these barriers is for the phase right
-                // after the last one observed
-                if (ok && upd)
-                    for (int jt = (ntl >= 2 ? ntl - 2 : 0); ok && jt < ntl; ++jt) {
-                        const unsigned g = c.g1 - (unsigned)(ntl - jt);
-                        if (!waitx(&sh->up_empty[g & 1], (g >> 1) & 1, 8, jt, sh, a)) ok = false;
-                    }
-                // (the release by MMA2 of the chunk's last tile)
-                if (ok && dots && ntl > 0 && !waitx(&sh->vp_empty, (c.g2 - 1) & 1, 11, ntl, sh, a)) ok = false;
                 // the commit arrives once every MMA issued above has completed
                 mma_commit(&sh->drained_a);
                 mbar_drain(&sh->drained_a, sh->flag[0] & 1, a.timeout_ns);
                 sh->flag[0]++;
                 TC5_ADD(sm, kTmMma, tm);
+            }
+            __syncwarp();
+        } else {
+            // ---------------- MMA2, one thread (warp kAllocWarp): the dots of tile i as soon as the
+            // epilogue has filled its four A slices; the V pieces are single-buffered (V(i + 1) is
+            // loaded once MMA2(i) has read V(i), a tile before MMA2(i + 1) needs it).
+            if (lane == 0 && dots) {
+                Counters c = cn;
+                const unsigned id2 = instr_desc(TR, PB);
+                const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+                auto load_vp = [&](int tile) {
+                    mbar_expect_tx(&sh->vp_full, kOp3);
+                    bulk_load(vp, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + tile), kOp3, &sh->vp_full);
+                };
+                load_vp(0);
+                for (int jt = 0; ok && jt < ntl; ++jt) {
+                    const unsigned b = c.g2 & 1;
+                    if (!waitx(&sh->vp_full, c.g2 & 1, 9, jt, sh, a) ||
+                        (c.g2 >= 2 && !waitx(&sh->d2_empty[b], ((c.g2 >> 1) - 1) & 1, 14, jt, sh, a))) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned d2 = tbase + kD2 + b * PB;
+                    for (int q = 0; q < NQ; ++q) {
+                        const unsigned sig = 4u * c.g2 + (unsigned)q;
+                        if (!waitx(&sh->as_full[q], c.g2 & 1, 10, jt, sh, a)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const unsigned char* asb = as + (sig % kNAs) * kOp3;
+                        const unsigned char* vb = vp + q * (PB * 32 * 2);
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                            for (int pq = 0; pq < 6; ++pq)
+                                mma_bf16(d2, smem_desc(asb + pa[pq] * kPiece + ks * (CW * 32)),
+                                         smem_desc(vb + pb[pq] * kPiece + ks * (PB * 32)), id2, (q | ks | pq) != 0);
+                        mma_commit(&sh->as_empty[(q + kNAs) % NQ]);   // the next user of this buffer
+                    }
+                    if (!ok) break;
+                    mma_commit(&sh->d2_full[b]);
+                    mma_commit(&sh->vp_empty);
+                    // V(jt + 1) once MMA2(jt) has read the buffer (every tile's release is waited for,
+                    // the last one after the loop)
+                    if (!waitx(&sh->vp_empty, c.g2 & 1, 11, jt, sh, a)) {
+                        ok = false;
+                        break;
+                    }
+                    if (jt + 1 < ntl) load_vp(jt + 1);
+                    c.g2++;
+                }
+                mma_commit(&sh->drained_b);
+                mbar_drain(&sh->drained_b, sh->flag[1] & 1, a.timeout_ns);
+                sh->flag[1]++;
             }
             __syncwarp();
         }
