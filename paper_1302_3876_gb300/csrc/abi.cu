@@ -58,7 +58,7 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, off_vpc, off_upc, total;
+        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, off_vpc, off_upc, off_ufc, off_wfin, total;
     int64_t ldp;              // row pitch of the 16-bit operand pieces (tensor-core panel modes)
     bool refine;
     // latched status of the previous call
@@ -192,6 +192,9 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
         p->off_P = o; o = align256(o + sizeof(double) * N * N);
         p->off_Md = o; o = align256(o + sizeof(double) * N * N);
         p->off_rnorm = o; o = align256(o + sizeof(double) * 1040);   // residual-norm partials + result
+        // the tensor-core solve's stored factors for its correction sweep
+        p->off_ufc = o; o = align256(o + (p->tc5 ? tc5_vpc_bytes(nobs, nens) : 0));
+        p->off_wfin = o; o = align256(o + (p->tc5 ? tc5_wfin_bytes(nens) : 0));
     }
     p->total = o;
     e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
@@ -380,6 +383,7 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         prof_end(p, slot, s);
     } else {
     PanelArgs panel_args;
+    bool solved_tc5 = false;
     if (p->mode == ENKF_PANEL_FP32 || p->mode == ENKF_PANEL_BF16 || p->mode == ENKF_PANEL_FP16 ||
         p->mode == ENKF_PANEL_BF16X3) {
         PanelArgs pa;
@@ -414,9 +418,11 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.ldp = p->ldp;
         cudaError_t et = cudaErrorNotSupported;
         if (p->tc5) {
-            et = tc5_solve(p->T5, pa, ws + p->off_vpc, ws + p->off_upc, s);
+            et = tc5_solve(p->T5, pa, ws + p->off_vpc, ws + p->off_upc, p->refine ? ws + p->off_ufc : nullptr,
+                           p->refine ? (float*)(ws + p->off_wfin) : nullptr, s);
             if (et == cudaErrorNotSupported) (void)cudaGetLastError();
             else CU(et, "tensor-core panel launch");
+            solved_tc5 = et == cudaSuccess;
         }
         if (et == cudaErrorNotSupported) CU(panel_launch(p->P, pa, s), "panel launch");
         panel_args = pa;
@@ -469,16 +475,26 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                 CU(refine_resid_norm(p->nobs, p->nens, delta, p->ldzw, (const float*)r, (const float*)D, ldd,
                                      (double*)(ws + p->off_rnorm), (double*)(ws + p->off_rnorm) + 1024, s),
                    "refine residual norm");
-            CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
-               "refine Gram V^T U");
             PanelArgs ra = panel_args;
-            ra.Qg = Q;
-            ra.refine = 1;
             ra.Z = delta;
             ra.ldz = p->ldzw;
-            ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
             CU(cudaMemsetAsync(&ctl->barrier, 0, sizeof(unsigned), s), "barrier reset");
-            CU(panel_launch(p->P, ra, s), "stored-factor correction");
+            cudaError_t ec = cudaErrorNotSupported;
+            if (solved_tc5) {
+                // the tensor-core solve's own stored factors (final-column pieces, per-panel
+                // diag(1/gamma) (I + L)^-1)
+                ec = tc5_correct(p->T5, ra, ws + p->off_vpc, ws + p->off_ufc, (const float*)(ws + p->off_wfin), s);
+                if (ec == cudaErrorNotSupported) (void)cudaGetLastError();
+                else CU(ec, "stored-factor correction (tensor cores)");
+            }
+            if (ec == cudaErrorNotSupported) {
+                CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
+                   "refine Gram V^T U");
+                ra.Qg = Q;
+                ra.refine = 1;
+                ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
+                CU(panel_launch(p->P, ra, s), "stored-factor correction");
+            }
             CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, ctl, a.timeout_ns, s),
                "refine Gram V^T delta");
             CU(refine_apply(p->nobs, p->nens, (float*)Zp, ldzp, delta, p->ldzw, P, Pd, M64, (float*)Mp, s),

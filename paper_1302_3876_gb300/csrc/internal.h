@@ -124,7 +124,13 @@ int tc5_panel_b();
 cudaError_t tc5_plan(int64_t nobs, int32_t nens, Tc5Launch* out);
 // Uses p.r, V, D, U, Z (and lds), part, coefg, C, gamma, ctl, check, timeout_ns.
 // cudaErrorNotSupported when U or Z is not TMA-aligned.
-cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, cudaStream_t s);
+cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, void* ufc, float* wfin,
+                      cudaStream_t s);
+// The stored factors of a tc5_solve applied to p.Z (the refinement's correction sweep);
+// workspace: ufc tc5_vpc_bytes, wfin tc5_wfin_bytes.
+cudaError_t tc5_correct(const Tc5Launch& L, const PanelArgs& p, const void* vpc, const void* ufc,
+                        const float* wfin, cudaStream_t s);
+size_t tc5_wfin_bytes(int32_t nens);
 
 // Q[k][m] = sum_j A[j,k] B[j,m] for k < m (strict upper triangle), split over rows,
 // partials in double; then Q = sum of the partials in a fixed order.

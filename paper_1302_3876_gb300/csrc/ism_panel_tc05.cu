@@ -143,6 +143,10 @@ struct Tc5Args {
     Control* ctl;
     int32_t check;
     uint64_t timeout_ns;
+    // stored factors for a later correction sweep (both null: not kept)
+    unsigned char* ufc;         // pieces of the final U columns of every panel: [panel][tile][24 KB]
+    float* wfin;                // per panel diag(1/gamma) (I + L)^-1: [panel][32][32]
+    int32_t refine;             // 1: apply the stored factors to Z (the correction sweep)
 };
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
@@ -204,6 +208,7 @@ struct SweepSpec {
     int ncols_prev;    // row stride of the previous sweep's reduced dots
     int mat;           // write the panel's final columns (MMA3)
     int up_par;        // parity of the U_P piece buffer holding panel P
+    const unsigned char* upb;   // MMA1's A pieces of panel P, tile 0 ([tile][24 KB])
 };
 
 __device__ __forceinline__ unsigned char* tile_piece(const unsigned char* base, int64_t index) {
@@ -526,6 +531,25 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                             if (h * HT + m < sp.bp)
                                 a.U[(int64_t)(sp.k0 + h * HT + m) * a.ldu + row] = __uint_as_float(u0[m]);
                     }
+                    if (a.ufc) {
+                        // their pieces in MMA1's A order, for the correction sweep
+                        unsigned char* fb = tile_piece(a.ufc, (int64_t)(sp.k0 / PB) * a.ntiles + T);
+#pragma unroll
+                        for (int g = 0; g < 2; ++g) {
+                            float v8[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int m = h * HT + g * 8 + e;
+                                v8[e] = (m < sp.bp && row < a.nobs) ? __uint_as_float(u0[g * 8 + e]) : 0.f;
+                            }
+                            uint4 pc[3];
+                            pieces8(v8, pc);
+#pragma unroll
+                            for (int pq = 0; pq < 3; ++pq)
+                                *reinterpret_cast<uint4*>(fb + pq * kPiece + kmaj_off(q * 32 + lane, 2 * h + g, TR * 32)) =
+                                    pc[pq];
+                        }
+                    }
                     fence_before();
                     mbar_arrive(&sh->d3_empty);
                 }
@@ -572,7 +596,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
                 auto load_up = [&](int tile) {
                     mbar_expect_tx(&sh->up_full[0], kOp3);
-                    bulk_load(up, tile_piece(a.upc, (int64_t)sp.up_par * a.ntiles + T0 + tile), kOp3, &sh->up_full[0]);
+                    bulk_load(up, tile_piece(sp.upb, T0 + tile), kOp3, &sh->up_full[0]);
                 };
                 load_up(0);
                 for (int it = 0; ok && it < ntl; ++it) {
@@ -725,6 +749,27 @@ __device__ bool reduce_tc5(const Tc5Args& a, Tc5Shared* sh, int nvals, unsigned&
     return okb;
 }
 
+// W_fin = diag(1/gamma) (I + L)^-1 of a factored panel, by one warp (lane l forms column l by
+// forward substitution, (I + L) t = e_l): with h_m = u_m / gamma_m the final columns, the
+// panel's b levels applied to any x are x <- x - U_fin W_fin (V_P^T x).
+__device__ void store_wfin(const FactorView& fv, int bp, float* out) {
+    const int l = threadIdx.x & 31;
+    float t[PB];
+#pragma unroll
+    for (int m = 0; m < PB; ++m) {
+        float v = (m == l) ? 1.f : 0.f;
+        if (m > l && m < bp) {
+#pragma unroll
+            for (int j = 0; j < m; ++j)
+                if (j >= l) v = fmaf(-fv.Lt[j * PB + m], t[j], v);
+        }
+        t[m] = (l < bp && m < bp) ? v : 0.f;
+    }
+#pragma unroll
+    for (int m = 0; m < PB; ++m)
+        out[m * PB + l] = (m < bp) ? t[m] * (float)(1.0 / fv.gam[m]) : 0.f;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __grid_constant__ CUtensorMap tmU,
                                                                      const __grid_constant__ CUtensorMap tmZ,
                                                                      Tc5Args a) {
@@ -775,16 +820,29 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
     const int N = a.nens, b = PB;
     Counters cn = {0u, 0u, 0u, 0u};
     unsigned epoch = 0;
-    // ---- the dots of panel 0 with every column of U^(0) = R^-1 V and Z^(0) = R^-1 D
-    // (Step 1, eq. SM-step-1, was applied by the pass before this launch)
+    // ---- the dots of panel 0: in the solve with every column of U^(0) = R^-1 V and Z^(0) =
+    // R^-1 D (Step 1, eq. SM-step-1, was applied by the pass before this launch); in the
+    // correction sweep with the columns of Z only (already scaled by R^-1)
+    const int kz = a.refine ? N : 0;                 // first trailing U column of the first sweep
     int nb = b < N ? b : N;
-    SweepSpec sp = {0, 0, 0, 0, nb, 0, 0, 0, 0};
-    bool ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, sp, cn) && reduce_tc5(a, sh, nb * 2 * N, epoch);
+    SweepSpec sp = {0, 0, kz, 0, nb, 0, 0, 0, 0, nullptr};
+    bool ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, sp, cn) && reduce_tc5(a, sh, nb * ((N - kz) + N), epoch);
     for (int k0 = 0; ok && k0 < N; k0 += b) {
         const int bp = (N - k0) < b ? (N - k0) : b;
         const int k1 = k0 + bp;
-        const int ncols_prev = (N - k0) + N;
+        const int pidx = k0 / b;
         TC5_T0(tf);
+        if (a.refine) {
+            // the panel's stored factor: K = -diag(1/gamma) (I + L)^-1 A applied to the final columns
+            for (int e = tid; e < PB * PB; e += kThreads) fv.W[e] = __ldcg(&a.wfin[(int64_t)pidx * PB * PB + e]);
+            nb = (N - k1) < b ? (N - k1) : b;
+            SweepSpec s2 = {k0, bp, N, k1, nb, 0, N, 0, 0, tile_piece(a.ufc, (int64_t)pidx * a.ntiles)};
+            ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, s2, cn);
+            if (ok && nb > 0) ok = reduce_tc5(a, sh, nb * N, epoch);
+            if (nb == 0) break;
+            continue;
+        }
+        const int ncols_prev = (N - k0) + N;
         // factor of the panel (every CTA): the FP64 Gram split into float hi + lo
         for (int e = tid; e < PB * PB; e += kThreads) {
             const int t = e / PB, u = e % PB;
@@ -816,11 +874,15 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
             }
             if (lane < bp) a.C[(int64_t)(k0 + lane) * N + i] = (double)v;
         }
+        // the stored factor for a correction sweep (the factor view is read before the sweep's
+        // second CTA barrier, after which the X slots it aliases are refilled)
+        if (a.wfin && blockIdx.x == 0 && warp == 0) store_wfin(fv, bp, a.wfin + (int64_t)pidx * PB * PB);
 #ifdef ENKF_TC5_TIMERS
         if (tid == 0) TC5_ADD(sm, kTmFac, tf);
 #endif
         nb = (N - k1) < b ? (N - k1) : b;
-        SweepSpec s2 = {k0, bp, k1, k1, nb, bp, ncols_prev, 1, (k0 / b) & 1};
+        const int par = pidx & 1;
+        SweepSpec s2 = {k0, bp, k1, k1, nb, bp, ncols_prev, 1, par, tile_piece(a.upc, (int64_t)par * a.ntiles)};
         ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, s2, cn);
         if (ok && nb > 0) ok = reduce_tc5(a, sh, nb * ((N - k1) + N), epoch);
         if (nb == 0) break;
@@ -987,8 +1049,10 @@ cudaError_t tc5_plan(int64_t nobs, int32_t nens, Tc5Launch* L) {
 
 // Step 1 and the tensor-core panel solve.  cudaErrorNotSupported when U or Z is not
 // TMA-aligned (16-byte base, stride a multiple of 4 floats): the caller then takes the
-// mma.sync panel kernel.
-cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, cudaStream_t s) {
+// mma.sync panel kernel.  ufc and wfin (both or neither): keep the final columns' pieces
+// and the per-panel factors for tc5_correct.
+cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, void* ufc, float* wfin,
+                      cudaStream_t s) {
     CUtensorMap tmU, tmZ;
     memset(&tmU, 0, sizeof(tmU));
     memset(&tmZ, 0, sizeof(tmZ));
@@ -1035,6 +1099,9 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
     a.ctl = p.ctl;
     a.check = p.check;
     a.timeout_ns = p.timeout_ns;
+    a.ufc = static_cast<unsigned char*>(ufc);
+    a.wfin = wfin;
+    a.refine = 0;
     if ((e = cudaFuncSetAttribute(ism_panel_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem)) !=
         cudaSuccess)
         return e;
@@ -1042,6 +1109,50 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
     return cudaLaunchCooperativeKernel((const void*)ism_panel_tc05_kernel, dim3(L.grid), dim3(kThreads), args, L.smem,
                                        s);
 }
+
+// The stored factors of a tc5_solve (its V pieces, final-column pieces ufc and per-panel
+// wfin) applied to p.Z, which holds R^-1 times a right-hand side: p.Z <- W^-1 R p.Z, the
+// levels of Step 2 in panel form with no U columns left to update.  p.U, p.coefg, p.part
+// and p.ctl as for the solve (U is not written); the grid-barrier word must be zero.
+cudaError_t tc5_correct(const Tc5Launch& L, const PanelArgs& p, const void* vpc, const void* ufc,
+                        const float* wfin, cudaStream_t s) {
+    CUtensorMap tmU, tmZ;
+    memset(&tmU, 0, sizeof(tmU));
+    memset(&tmZ, 0, sizeof(tmZ));
+    if (!encode_f32_2d(&tmU, static_cast<const float*>(p.U), p.nobs, p.nens, p.ldu, 32, SWC, true) ||
+        !encode_f32_2d(&tmZ, static_cast<const float*>(p.Z), p.nobs, p.nens, p.ldz, 32, SWC, true))
+        return cudaErrorNotSupported;
+    Tc5Args a;
+    memset(&a, 0, sizeof(a));
+    a.nobs = p.nobs;
+    a.nens = p.nens;
+    a.ntiles = L.ntiles;
+    a.tiles_per_blk = L.tiles_per_blk;
+    a.r = static_cast<const float*>(p.r);
+    a.U = static_cast<float*>(p.U);
+    a.ldu = p.ldu;
+    a.Z = static_cast<float*>(p.Z);
+    a.ldz = p.ldz;
+    a.vpc = static_cast<const unsigned char*>(vpc);
+    a.part = p.part;
+    a.part_stride = L.part_stride;
+    a.coefg = p.coefg;
+    a.ctl = p.ctl;
+    a.check = 0;
+    a.timeout_ns = p.timeout_ns;
+    a.ufc = const_cast<unsigned char*>(static_cast<const unsigned char*>(ufc));
+    a.wfin = const_cast<float*>(wfin);
+    a.refine = 1;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ism_panel_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem)) !=
+        cudaSuccess)
+        return e;
+    void* args[] = {&tmU, &tmZ, &a};
+    return cudaLaunchCooperativeKernel((const void*)ism_panel_tc05_kernel, dim3(L.grid), dim3(kThreads), args, L.smem,
+                                       s);
+}
+
+size_t tc5_wfin_bytes(int32_t nens) { return (size_t)((nens + PB - 1) / PB) * PB * PB * sizeof(float); }
 
 }  // namespace enkf
 
