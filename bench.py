@@ -1,23 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the iterative Sherman-Morrison EnKF analysis on one GB300.
 
-Workload (default): the large single analysis -- Nstate = 2^21, Nobs = 2^19
-(every 4th state variable observed), Nens = 128; deviations dX_B[i,e] = s_i N(0,1)
-with s_i ~ U[0.5, 2], variances r_j ~ U[0.5, 1.5], innovations D ~ N(0,1), and the
-background equal to the deviations.  One step = the whole analysis through the C
-ABI: V = H dX_B / sqrt(Nens-1) on the device, Step 1 + Step 2 of the iterative
-Sherman-Morrison formula, M = V^T Z / sqrt(Nens-1), X_A = X_B + dX_B M.  Inputs
-(1.3 GB) are larger than L2, so no flush is needed between steps.
+Workload (default): the panel workload -- Nstate = 2^22, Nobs = 2^20 (every 4th
+state variable observed), Nens = 256; deviations dX_B[i,e] = s_i N(0,1) with
+s_i ~ U[0.5, 2], variances r_j ~ U[0.5, 1.5], innovations D ~ N(0,1), and the
+background equal in value to the deviations but held in a buffer of its own.
+``--workload large_single`` takes Nstate = 2^21, Nobs = 2^19, Nens = 128.  One step
+= the whole analysis through the C ABI: V = H dX_B / sqrt(Nens-1) on the device,
+Step 1 + Step 2 of the iterative Sherman-Morrison formula, one step of iterative
+refinement, M = V^T Z / sqrt(Nens-1), X_A = X_B + dX_B M.  Inputs (several GB) are
+larger than L2, so no flush is needed between steps.
 
-The headline path is the panel form on FP32 CUDA cores (32 levels per pass,
-FP64 denominators; ``--mode`` selects the tensor-core panel variants or the plain
-FP32 level-streaming path); the FP64 plain path is timed in the same run as the
-comparator.  ``--impl reference`` times the FP64 CPU oracle instead (bounded
-sample of the same workload).  Other workloads (``--workload``): the panel
-workload at Nstate 2^22 / Nobs 2^20 / 256 members, the batched local analyses,
-the Lorenz-96 cycle with the learned surrogate, and the rows beside the analysis
-(inflation, partial localization, block-diagonal R, pivoting); each prints its
-own JSON line.
+The headline path is the panel form on tcgen05 tensor cores (32 levels per pass,
+operands split in three BF16 pieces, FP64-class denominators) with one refinement
+step (``--mode`` selects the other panel variants or the plain FP32 level-streaming
+path, ``--no-refine`` drops the refinement); the FP64 plain path is timed in the
+same run as the comparator, with the errors of every result against it.
+``--impl reference`` times the FP64 CPU oracle instead (bounded sample of the same
+workload).  Other workloads (``--workload``): the batched local analyses, the
+single Lorenz-96 analysis (one call and CUDA-graph replays), the Lorenz-96 cycle
+with the learned surrogate, and the rows beside the analysis (inflation, partial
+localization, block-diagonal R, pivoting); each prints its own JSON line.
 
 Prints ONE JSON line on rank 0.
 """
@@ -67,6 +70,27 @@ def panel_bytes(nobs, nens, b, w):
         nb = min(b, max(0, nens - k0 - bp))
         cols += 2 * (2 * nens - k0 - bp) + bp + nb + 2 * bp
     return w * nobs * cols
+
+
+def correction_bytes(nobs, nens, b, w):
+    """Algorithmic bytes of the refinement's correction sweep (the tensor-core kernel with
+    the stored factors): the first pass reads the N columns of the scaled residual and b
+    columns of V; panel p reads and writes the N columns, reads its b final U columns and
+    the next b columns of V."""
+    cols = nens + b
+    for k0 in range(0, nens, b):
+        bp = min(b, nens - k0)
+        nb = min(b, max(0, nens - k0 - bp))
+        cols += 2 * nens + bp + nb
+    return w * nobs * cols
+
+
+def read_bf16_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"])
+    except Exception:  # noqa: BLE001
+        return 1700.0
 
 
 def measure_fma_peaks(dev, local):
@@ -282,7 +306,8 @@ MODES = {"panel32": "ENKF_PANEL_FP32", "bf16": "ENKF_PANEL_BF16", "fp16": "ENKF_
          "bf16x3": "ENKF_PANEL_BF16X3", "fp32": "ENKF_FP32"}
 PATH_NAME = {"panel32": "panel form on FP32 CUDA cores, b=%d (FP64 gamma)",
              "bf16": "panel form on tensor cores, split BF16 operands, b=%d (FP64 gamma)",
-             "bf16x3": "panel form on tensor cores, BF16 operands split in three, b=%d (FP64 gamma)",
+             "bf16x3": "panel form on tcgen05 tensor cores (TMEM accumulators, TMA), BF16 operands split in three, "
+                       "b=%d (FP64-class gamma)",
              "fp16": "panel form on tensor cores, FP16 operands, b=%d (FP64 gamma)",
              "fp32": "FP32 plain level-streaming (FP64 gamma and cross-CTA sums)"}
 
@@ -492,6 +517,33 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": lv_avg,
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_stream.cu"),
                                                f"ism_levels_{args.workload}_fp32.md")}
+    elif args.mode == "bf16x3" and "panel_kernel" in phases:
+        # the tcgen05 panel kernel alone (phase 6: CUDA events around its launch inside the step)
+        k_ms, k_n = phases["panel_kernel"]
+        k_avg = k_ms / max(k_n, 1)
+        pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
+        achieved = pb / (k_avg / 1e3) / 1e9
+        bf16_sus = read_bf16_sustained()
+        t_flops = 6 * f_solve      # six BF16 products per FP32 multiply-add of the trailing update and dots
+        roofline = {"kernel": "ism_panel_tc05_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                    "algorithmic_bytes_per_launch": pb, "avg_launch_ms": k_avg,
+                    "tensor_view": {"tensor_flops_per_launch": t_flops,
+                                    "achieved_tflops": t_flops / (k_avg / 1e3) / 1e12,
+                                    "peak_tflops": bf16_sus,
+                                    "frac": t_flops / (k_avg / 1e3) / 1e12 / bf16_sus,
+                                    "peak_kind": "measured (MEASURED_PEAKS bf16_tflops_sustained: the kernel is "
+                                                 "timed inside a long step)"},
+                    "traffic": profile_traffic(os.path.join(src_dir, "ism_panel_tc05.cu"),
+                                               f"ism_panel_tc05_{args.workload}.md")}
+        if "correction_kernel" in phases:
+            c_ms, c_n = phases["correction_kernel"]
+            c_avg = c_ms / max(c_n, 1)
+            cb = correction_bytes(NOBS, NENS, args.panel_b, 4)
+            roofline["correction_launch"] = {
+                "kernel": "ism_panel_tc05_kernel (correction sweep)", "algorithmic_bytes_per_launch": cb,
+                "avg_launch_ms": c_avg, "achieved_gbs": cb / (c_avg / 1e3) / 1e9,
+                "frac": cb / (c_avg / 1e3) / 1e9 / peak}
     elif args.mode in ("bf16", "fp16", "bf16x3"):
         pb = panel_bytes(NOBS, NENS, args.panel_b, 4)
         achieved = pb / (lv_avg / 1e3) / 1e9
@@ -518,7 +570,8 @@ def run_ours(args):
                                  "peak_gbs": peak, "frac": pb / (lv_avg / 1e3) / 1e9 / peak},
                     "traffic": profile_traffic(os.path.join(src_dir, "ism_panel.cu"),
                                                f"ism_panel_{args.workload}_fp32.md")}
-    total_ms = sum(v[0] for v in phases.values())
+    inner = ("panel_kernel", "correction_kernel")      # kernels timed inside other phases
+    total_ms = sum(v[0] for k, v in phases.items() if k not in inner)
     ms_step = t_max / args.steps
     launches = 1 + 1 + (14 if refine else 5)
     line = {
@@ -538,7 +591,7 @@ def run_ours(args):
                            "sm_mhz_during": peaks["sm_mhz"], "hbm_gbs": peak,
                            "bf16_tflops": read_bf16_peak(), "how": peaks["how"]},
         "phases_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in phases.items()},
-        "phase_share": {k: v[0] / total_ms for k, v in phases.items()} if total_ms > 0 else {},
+        "phase_share": {k: v[0] / total_ms for k, v in phases.items() if k not in inner} if total_ms > 0 else {},
         "e2e": None if args.no_e2e else {
             "value": world / (e2e_ms / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
@@ -1002,17 +1055,17 @@ def run_next_rows(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["panel32", "bf16", "fp16", "bf16x3", "fp32"], default="panel32",
-                    help="headline path: panel form on FP32 CUDA cores (panel32), on tensor cores with split BF16 "
-                         "(bf16), three-piece BF16 (bf16x3) or FP16 (fp16) operands, or the FP32 level-streaming "
-                         "path (fp32)")
+    ap.add_argument("--mode", choices=["panel32", "bf16", "fp16", "bf16x3", "fp32"], default="bf16x3",
+                    help="headline path: panel form on tcgen05 tensor cores with three-piece BF16 operands (bf16x3, "
+                         "default), on FP32 CUDA cores (panel32), on mma.sync tensor cores with split BF16 (bf16) or "
+                         "FP16 (fp16) operands, or the FP32 level-streaming path (fp32)")
     ap.add_argument("--panel-b", type=int, default=32)
     ap.add_argument("--refine", action=argparse.BooleanOptionalAction, default=True,
                     help="one step of iterative refinement (panel modes; on by default: the refined FP32 path is "

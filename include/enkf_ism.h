@@ -389,7 +389,9 @@ ENKF_API enkf_status enkf_ism_solve_pivot(int64_t nobs, int32_t nens, int32_t pr
  * the elapsed milliseconds of each phase into ms[phase] and the number of
  * launches into count[phase] (arrays of ENKF_PROFILE_PHASES, caller-owned host
  * memory), and clears the record.  Phases: 0 obs prep, 1 level streaming (Step 1
- * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update, 5 refinement.
+ * and Step 2), 2 Gram V^T U, 3 assembly of M, 4 X_A update, 5 refinement; and two
+ * kernels inside those phases, each timed alone: 6 the panel kernel of phase 1
+ * (panel modes), 7 the refinement's correction sweep (inside phase 5).
  */
 /*
  * enkf_ism_gamma -- the level denominators gamma_k = 1 + v_k^T u_k^(k-1), k = 1..nens

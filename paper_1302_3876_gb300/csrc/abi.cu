@@ -87,6 +87,15 @@ int prof_begin(enkf_ism_plan_s* p, int phase, cudaStream_t s) {
 void prof_end(enkf_ism_plan_s* p, int slot, cudaStream_t s) {
     if (slot >= 0) cudaEventRecord(p->prof_ev[2 * slot + 1], s);
 }
+
+// A phase slot whose two events the caller records itself (around one launch inside a
+// phase); -1 when profiling is off or the record is full.
+int prof_reserve(enkf_ism_plan_s* p, int phase) {
+    if (!p->prof || p->nprof >= kProfCap) return -1;
+    const int i = p->nprof++;
+    p->prof_phase[i] = phase;
+    return i;
+}
 }  // namespace
 
 extern "C" {
@@ -239,8 +248,10 @@ enkf_status enkf_ism_profile(enkf_ism_plan_t p, int32_t enable) {
 
 enkf_status enkf_ism_profile_read(enkf_ism_plan_t p, double* ms, int32_t* count) {
     if (!p || !ms || !count) return fail(ENKF_ERR_ARG, "enkf_ism_profile_read: NULL argument");
-    if (p->nprof > 0) CU(cudaEventSynchronize(p->prof_ev[2 * (p->nprof - 1) + 1]), "cudaEventSynchronize");
     for (int i = 0; i < p->nprof; ++i) {
+        // phases nest (a kernel's own slot inside its phase), so the last slot is not always
+        // the last event recorded: wait for each
+        CU(cudaEventSynchronize(p->prof_ev[2 * i + 1]), "cudaEventSynchronize");
         float t = 0.f;
         CU(cudaEventElapsedTime(&t, p->prof_ev[2 * i], p->prof_ev[2 * i + 1]), "cudaEventElapsedTime");
         const int ph = p->prof_phase[i];
@@ -418,13 +429,20 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
         pa.ldp = p->ldp;
         cudaError_t et = cudaErrorNotSupported;
         if (p->tc5) {
+            const int k6 = prof_reserve(p, 6);
             et = tc5_solve(p->T5, pa, ws + p->off_vpc, ws + p->off_upc, p->refine ? ws + p->off_ufc : nullptr,
-                           p->refine ? (float*)(ws + p->off_wfin) : nullptr, s);
+                           p->refine ? (float*)(ws + p->off_wfin) : nullptr, s, k6 >= 0 ? p->prof_ev[2 * k6] : nullptr,
+                           k6 >= 0 ? p->prof_ev[2 * k6 + 1] : nullptr);
+            if (et != cudaSuccess && k6 >= 0) --p->nprof;      // nothing was recorded in the slot
             if (et == cudaErrorNotSupported) (void)cudaGetLastError();
             else CU(et, "tensor-core panel launch");
             solved_tc5 = et == cudaSuccess;
         }
-        if (et == cudaErrorNotSupported) CU(panel_launch(p->P, pa, s), "panel launch");
+        if (et == cudaErrorNotSupported) {
+            const int k6 = prof_begin(p, 6, s);
+            CU(panel_launch(p->P, pa, s), "panel launch");
+            prof_end(p, k6, s);
+        }
         panel_args = pa;
     } else {
         CU(level_launch(p->fp64, p->L, a, s), "level-streaming launch");
@@ -483,7 +501,9 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             if (solved_tc5) {
                 // the tensor-core solve's own stored factors (final-column pieces, per-panel
                 // diag(1/gamma) (I + L)^-1)
+                const int k7 = prof_begin(p, 7, s);
                 ec = tc5_correct(p->T5, ra, ws + p->off_vpc, ws + p->off_ufc, (const float*)(ws + p->off_wfin), s);
+                prof_end(p, k7, s);
                 if (ec == cudaErrorNotSupported) (void)cudaGetLastError();
                 else CU(ec, "stored-factor correction (tensor cores)");
             }
@@ -493,7 +513,9 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                 ra.Qg = Q;
                 ra.refine = 1;
                 ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
+                const int k7 = prof_begin(p, 7, s);
                 CU(panel_launch(p->P, ra, s), "stored-factor correction");
+                prof_end(p, k7, s);
             }
             CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, ctl, a.timeout_ns, s),
                "refine Gram V^T delta");

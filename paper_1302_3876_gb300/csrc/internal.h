@@ -125,7 +125,7 @@ cudaError_t tc5_plan(int64_t nobs, int32_t nens, Tc5Launch* out);
 // Uses p.r, V, D, U, Z (and lds), part, coefg, C, gamma, ctl, check, timeout_ns.
 // cudaErrorNotSupported when U or Z is not TMA-aligned.
 cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, void* ufc, float* wfin,
-                      cudaStream_t s);
+                      cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // The stored factors of a tc5_solve applied to p.Z (the refinement's correction sweep);
 // workspace: ufc tc5_vpc_bytes, wfin tc5_wfin_bytes.
 cudaError_t tc5_correct(const Tc5Launch& L, const PanelArgs& p, const void* vpc, const void* ufc,

@@ -1050,9 +1050,10 @@ cudaError_t tc5_plan(int64_t nobs, int32_t nens, Tc5Launch* L) {
 // Step 1 and the tensor-core panel solve.  cudaErrorNotSupported when U or Z is not
 // TMA-aligned (16-byte base, stride a multiple of 4 floats): the caller then takes the
 // mma.sync panel kernel.  ufc and wfin (both or neither): keep the final columns' pieces
-// and the per-panel factors for tc5_correct.
+// and the per-panel factors for tc5_correct.  ev0 / ev1 (optional): recorded around the
+// panel kernel alone (phase timing).
 cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* upc, void* ufc, float* wfin,
-                      cudaStream_t s) {
+                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
     CUtensorMap tmU, tmZ;
     memset(&tmU, 0, sizeof(tmU));
     memset(&tmZ, 0, sizeof(tmZ));
@@ -1106,8 +1107,10 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
         cudaSuccess)
         return e;
     void* args[] = {&tmU, &tmZ, &a};
-    return cudaLaunchCooperativeKernel((const void*)ism_panel_tc05_kernel, dim3(L.grid), dim3(kThreads), args, L.smem,
-                                       s);
+    if (ev0) cudaEventRecord(ev0, s);
+    e = cudaLaunchCooperativeKernel((const void*)ism_panel_tc05_kernel, dim3(L.grid), dim3(kThreads), args, L.smem, s);
+    if (ev1) cudaEventRecord(ev1, s);
+    return e;
 }
 
 // The stored factors of a tc5_solve (its V pieces, final-column pieces ufc and per-panel

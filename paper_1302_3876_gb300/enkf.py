@@ -41,7 +41,8 @@ ENKF_FORECAST_RK4 = 0
 ENKF_FORECAST_SURROGATE = 1
 
 ENKF_PROFILE_PHASES = 8
-PROFILE_PHASE_NAMES = ("obs_prep", "ism_solve", "gram_upper", "assemble_M", "xa_update", "refine", "", "")
+PROFILE_PHASE_NAMES = ("obs_prep", "ism_solve", "gram_upper", "assemble_M", "xa_update", "refine", "panel_kernel",
+                       "correction_kernel")
 
 
 class EnkfError(RuntimeError):
