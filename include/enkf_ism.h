@@ -110,6 +110,8 @@ typedef struct {
 
 /*
  * enkf_ism_plan -- validate sizes and choose launch shapes for one problem size.
+ * Infrastructure around the method (no passage of the paper defines it): it fixes the
+ * launch shapes of the analysis of Sec. 3.1 and the size of the caller's workspace.
  *
  *   out              receives the plan (host object; free with enkf_ism_plan_destroy).
  *   nstate           state dimension (rows of X_B, dX_B, X_A); >= 1.
@@ -118,8 +120,9 @@ typedef struct {
  *                    the solve only (M and X_A need nens >= 2, since S divides
  *                    by sqrt(Nens - 1)).
  *   mode             an enkf_mode.
- *   panel_b          panel width for the panel modes (0 = default 32; 1 <= panel_b <= 32);
- *                    ignored otherwise.
+ *   panel_b          panel width for the panel modes (0 = default 32; 1 <= panel_b <= 32,
+ *                    else ENKF_ERR_ARG); ignored otherwise.  ENKF_PANEL_BF16X3 with b = 32
+ *                    runs the tcgen05 panel kernel when U and Z are TMA-aligned.
  *   flags            ENKF_FLAG_* bits.
  *   workspace_bytes  receives the device workspace size enkf_ism_analysis needs.
  *
@@ -454,6 +457,49 @@ ENKF_API enkf_status enkf_ism_solve_noalloc(int64_t nobs, int32_t nens, int32_t 
  */
 ENKF_API enkf_status enkf_fma_peak_launch(int32_t precision, int32_t iters, int32_t ctas_per_sm, void* sink,
                                           void* stream, double* flops);
+
+/*
+ * Row-sharded analysis: the data path of one block of observation rows.  The rows of
+ * V, D, U, Z and r are split into blocks (one per rank; every rank holds all N columns
+ * of its rows).  Step 1 (Sec. 3.1, eq. SM-step-1) is local to a block; level k of Step 2
+ * (eqs. SM-step-2-h/Z/u) needs the dots of v_k with z_0..z_{N-1} and u_k..u_{N-1} summed
+ * over every block, which the caller forms by summing the blocks' partial dots (one
+ * all-reduce of 2N doubles per level); every block then applies the level to its own
+ * rows.  Sequence per rank (arrays: device memory, column-major, caller-owned):
+ *   enkf_rows_level(k = -1)            U = R^-1 V, Z = R^-1 D on the block, and the block's
+ *                                      partial dots of level 0 into part;
+ *   for k = 0 .. N-1:  coef <- sum over ranks of part;
+ *     enkf_rows_level(k)               level k on the block with the reduced dots coef
+ *                                      (records C[k][:] = coef[0..N), gamma[k] = 1 +
+ *                                      coef[N + k]), and the partial dots of level k + 1;
+ *   enkf_rows_gram                     the block's partial Q[k][m] = v_k^T u_m (k < m) of the
+ *                                      final U columns; Q <- sum over ranks;
+ *   enkf_rows_assemble                 M = (I - triu(Q,1)) diag(1/gamma) C / sqrt(N - 1)
+ *                                      (= V^T Z / sqrt(N - 1), Sec. 3.1) on every rank;
+ *   enkf_rows_xa                       X_A = X_B + dX_B M on the rank's block of state rows.
+ * coef and part: 2N doubles, entry i = v_k^T z_i, entry N + i = v_k^T u_i (i >= k; the
+ * other entries of part are zero).  C: N x N doubles (row k = level k), gamma: N doubles.
+ * precision ENKF_FP64 or ENKF_FP32 (element type of r, V, D, U, Z, X_B, dX_B, X_A, M);
+ * dots, C, gamma and Q are FP64.  Each call launches on `stream` and returns; device-side
+ * checks (r_j <= 0, non-finite values, gamma_k < 1 - tol) latch a status word in the
+ * workspace (cleared by the k = -1 call) that enkf_rows_status reads (synchronising the
+ * stream).  Workspace: enkf_rows_workspace(nobs, nens) bytes, one per rank and stream.
+ * Errors: ENKF_ERR_ARG (NULL or out-of-range argument), ENKF_ERR_SHAPE (sizes, leading
+ * dimensions), ENKF_ERR_WORKSPACE, ENKF_ERR_CUDA.
+ */
+ENKF_API enkf_status enkf_rows_workspace(int64_t nobs, int32_t nens, size_t* bytes);
+ENKF_API enkf_status enkf_rows_level(int32_t precision, int64_t nobs, int32_t nens, int32_t k, const void* r,
+                                     const void* V, int64_t ldv, const void* D, int64_t ldd, void* U, int64_t ldu,
+                                     void* Z, int64_t ldz, const double* coef, double* C, double* gamma,
+                                     double* part, void* workspace, size_t workspace_bytes, void* stream);
+ENKF_API enkf_status enkf_rows_gram(int32_t precision, int64_t nobs, int32_t nens, const void* V, int64_t ldv,
+                                    const void* U, int64_t ldu, double* Q, void* workspace, size_t workspace_bytes,
+                                    void* stream);
+ENKF_API enkf_status enkf_rows_assemble(int32_t precision, int32_t nens, const double* Q, const double* C,
+                                        const double* gamma, void* M, void* stream);
+ENKF_API enkf_status enkf_rows_xa(int32_t precision, int64_t nstate, int32_t nens, const void* XB, int64_t ldb,
+                                  const void* dXB, int64_t ldx, const void* M, void* XA, int64_t lda, void* stream);
+ENKF_API enkf_status enkf_rows_status(void* workspace, void* stream, int32_t* status);
 
 /* Human-readable name of a status code (static string). */
 ENKF_API const char* enkf_status_string(enkf_status s);

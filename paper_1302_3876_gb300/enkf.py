@@ -120,6 +120,19 @@ def load(build_if_missing: bool = False):
         lib.enkf_rblock_whiten.restype = ctypes.c_int
         lib.enkf_rblock_unwhiten.argtypes = [i64, i32, i32, i32, vp, vp, i64, vp]
         lib.enkf_rblock_unwhiten.restype = ctypes.c_int
+        lib.enkf_rows_workspace.argtypes = [i64, i32, ctypes.POINTER(sz)]
+        lib.enkf_rows_workspace.restype = ctypes.c_int
+        lib.enkf_rows_level.argtypes = [i32, i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, vp,
+                                        vp, sz, vp]
+        lib.enkf_rows_level.restype = ctypes.c_int
+        lib.enkf_rows_gram.argtypes = [i32, i64, i32, vp, i64, vp, i64, vp, vp, sz, vp]
+        lib.enkf_rows_gram.restype = ctypes.c_int
+        lib.enkf_rows_assemble.argtypes = [i32, i32, vp, vp, vp, vp, vp]
+        lib.enkf_rows_assemble.restype = ctypes.c_int
+        lib.enkf_rows_xa.argtypes = [i32, i64, i32, vp, i64, vp, i64, vp, vp, i64, vp]
+        lib.enkf_rows_xa.restype = ctypes.c_int
+        lib.enkf_rows_status.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        lib.enkf_rows_status.restype = ctypes.c_int
         lib.enkf_ism_pivot_workspace.argtypes = [i64, i32, i32, ctypes.POINTER(sz)]
         lib.enkf_ism_pivot_workspace.restype = ctypes.c_int
         lib.enkf_ism_solve_pivot.argtypes = [i64, i32, i32, vp, vp, i64, vp, i64, vp, i64, vp, vp, vp, vp, sz, vp,
@@ -321,6 +334,58 @@ def enkf_rblock_unwhiten(bs: int, Lblk, Z, stream=None) -> None:
     pZ, ldz = _mat(Z, "Z")
     ncols, nobs = Z.shape
     _check(load().enkf_rblock_unwhiten(nobs, ncols, _precision(Z), bs, _ptr(Lblk, "Lblk"), pZ, ldz, _stream(stream)))
+
+
+def enkf_rows_workspace(nobs: int, nens: int) -> int:
+    b = ctypes.c_size_t()
+    _check(load().enkf_rows_workspace(nobs, nens, ctypes.byref(b)))
+    return b.value
+
+
+def enkf_rows_level(k: int, r, V, D, U, Z, coef, C, gamma, part, workspace, stream=None) -> None:
+    """Level k of Step 2 on a block of rows (k = -1: Step 1); V, D, U, Z: (nens, nobs) tensors,
+    r: (nobs,), coef / part: (2 nens,) float64, C: (nens, nens) float64, gamma: (nens,) float64."""
+    pV, ldv = _mat(V, "V")
+    pD, ldd = _mat(D, "D")
+    pU, ldu = _mat(U, "U")
+    pZ, ldz = _mat(Z, "Z")
+    nens, nobs = V.shape[0], V.shape[1]
+    _check(load().enkf_rows_level(_precision(V), nobs, nens, k, _ptr(r, "r"), pV, ldv, pD, ldd, pU, ldu, pZ, ldz,
+                                  _ptr(coef, "coef"), _ptr(C, "C"), _ptr(gamma, "gamma"), _ptr(part, "part"),
+                                  _ptr(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                                  _stream(stream)))
+
+
+def enkf_rows_gram(V, U, Q, workspace, stream=None) -> None:
+    """The block's partial Q[k][m] = v_k^T u_m (k < m) into Q ((nens, nens) float64, row-major [k][m])."""
+    pV, ldv = _mat(V, "V")
+    pU, ldu = _mat(U, "U")
+    nens, nobs = V.shape[0], V.shape[1]
+    _check(load().enkf_rows_gram(_precision(V), nobs, nens, pV, ldv, pU, ldu, _ptr(Q, "Q"), _ptr(workspace, "workspace"),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def enkf_rows_assemble(Q, C, gamma, M, stream=None) -> None:
+    """M = (I - triu(Q,1)) diag(1/gamma) C / sqrt(N - 1); M: (nens * nens,) of the storage precision."""
+    nens = gamma.shape[0]
+    _check(load().enkf_rows_assemble(_precision(M), nens, _ptr(Q, "Q"), _ptr(C, "C"), _ptr(gamma, "gamma"),
+                                     _ptr(M, "M"), _stream(stream)))
+
+
+def enkf_rows_xa(XB, dXB, M, XA, stream=None) -> None:
+    """X_A = X_B + dX_B M on a block of state rows (XB, dXB, XA: (nens, nstate_block))."""
+    pXB, ldb = _mat(XB, "XB")
+    pdX, ldx = _mat(dXB, "dXB")
+    pXA, lda = _mat(XA, "XA")
+    nens, nstate = dXB.shape[0], dXB.shape[1]
+    _check(load().enkf_rows_xa(_precision(dXB), nstate, nens, pXB, ldb, pdX, ldx, _ptr(M, "M"), pXA, lda,
+                               _stream(stream)))
+
+
+def enkf_rows_status(workspace, stream=None) -> int:
+    st = ctypes.c_int32(0)
+    _check(load().enkf_rows_status(_ptr(workspace, "workspace"), _stream(stream), ctypes.byref(st)))
+    return st.value
 
 
 def enkf_ism_pivot_workspace(nobs: int, nens: int, precision: int) -> int:

@@ -113,6 +113,10 @@ LOC_CASES = [
     (777, 3, 33, math.inf, None),   # delta = 1: the unlocalized update
     (300, 5, 8, 20.0, 0.0),         # radius 0: only the observed components move
     (130, 1, 64, 40.0, 64.0),       # band wider than the ring: dense visit with a cut-off
+    # the band shapes that tests/test_localize_band.py checks on the CPU, on the kernel itself:
+    # tile 0 and the partial last tile wrap around the ring
+    (97, 3, 12, 20.0, 31.9),
+    (64, 1, 9, 8.0, 15.9),
 ]
 
 
