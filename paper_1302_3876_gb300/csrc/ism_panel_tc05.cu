@@ -18,19 +18,28 @@
 // Data flow of one sweep, per CTA (one per SM; the CTA owns a block of 128-row tiles):
 //   column chunks of 128 trailing columns (U part and Z part apart), and within a chunk
 //   every tile of the CTA:
-//   - X: four epilogue warps, one per 32-row quarter of the tile, each with a ring of
-//     four slots of 32 rows x 32 columns FP32 (TMA, 128-byte swizzle); a warp refills a
-//     slot with the next tile's block as soon as it is done with it.
-//   - U_P pieces (two buffers) and V_{P'} pieces (one): 24 KB per tile each, laid out in global memory in the
-//     canonical K-major order of the MMA operands (written once per panel by the
-//     previous sweep, or by the Step-1 pass for V) and brought in by one bulk copy.
-//   - K (and beta) pieces: computed per chunk (per sweep) by the whole CTA.
-//   - the epilogue adds MMA1's TMEM accumulator to X, stores X_new, writes it back to
-//     its slot, then converts its 32 rows into the pieces of MMA2's A operand (K-major:
-//     each column's 8 consecutive rows in 16 bytes); warp 4 issues MMA1 and MMA3, warp 5
-//     MMA2, each with its own commits.
+//   - X: eight epilogue warps, warp (q, h) for the 32-row quarter q of the tile and the
+//     column half h, each with two slots of 32 rows x 32 columns FP32 (TMA, 128-byte
+//     swizzle), refilled with the next tile's block as soon as the warp is done with it.
+//   - U_P pieces and V_{P'} pieces: 24 KB per tile each (one buffer each), laid out in
+//     global memory in the canonical K-major order of the MMA operands (written once per
+//     panel by the previous sweep, or by the Step-1 pass for V) and brought in by one
+//     bulk copy.
+//   - K (and beta) pieces: computed per chunk by the whole CTA.
+//   - per tile the epilogue warp (1) adds MMA1's TMEM accumulator to its slots, writes
+//     X_new back to the slots and stores them with TMA, and releases D1; (2) waits for
+//     its A-slice buffer (three buffers rotate over the four quarters); (3) converts its
+//     rows into the pieces of MMA2's A operand (K-major: each column's 8 consecutive rows
+//     in 16 bytes) and refills its slots; then writes the panel's final columns (MMA3)
+//     and folds the previous tile's dots (MMA2's TMEM accumulator) into registers.
+//   - warp 8 issues MMA1 and MMA3 and loads U_P; warp 9 issues MMA2 as each A slice
+//     fills and loads V; each with its own commits.
 // TMEM: D1 (MMA1, two buffers of 128 columns) at 0 and 128, D2 (MMA2, two buffers of 32)
 // at 256 and 288, D3 (MMA3) at 320.
+//
+// The refinement's correction sweep runs in the same kernel (Tc5Args::refine): the solve
+// keeps the pieces of every panel's final columns u_m and diag(1/gamma) (I + L)^-1, and the
+// correction applies them to the columns of Z alone, with no factor and no U part.
 //
 // Every wait is bounded (iteration count and %globaltimer); on expiry the CTA latches
 // ENKF_ERR_TIMEOUT, drains its copies and MMAs with bounded waits, frees TMEM and returns;
@@ -56,7 +65,9 @@ constexpr int SWC = 32;              // columns per X slot
 constexpr int NQ = 4;                // epilogue warps (row quarters)
 constexpr int NS = CW / SWC;         // slots per epilogue warp
 constexpr int PB = 32;               // panel width (MMA2 N, MMA1 K)
-constexpr int NEPI = 2 * NQ;         // epilogue warps: row quarter w % 4, column half w / 4
+constexpr int NH = 2;                // column groups of the epilogue warps
+constexpr int NEPI = NQ * NH;        // epilogue warps: row quarter w % 4, column group w / 4
+constexpr int NSW = NS / NH;         // X slots per epilogue warp
 constexpr int kMmaWarp = NEPI, kAllocWarp = NEPI + 1;
 constexpr int kThreads = 32 * (NEPI + 2);
 constexpr int kSlotBytes = SWC * 32 * 4;          // 32 columns x 32 rows FP32 (4 KB)
@@ -64,7 +75,10 @@ constexpr int kPiece = TR * PB * 2;               // one BF16 piece of a 128 x 3
 constexpr int kOp3 = 3 * kPiece;                  // the three pieces (24 KB)
 constexpr int kBeta3 = 3 * PB * PB * 2;           // beta pieces (6 KB)
 constexpr unsigned kTmemCols = 512;
-constexpr unsigned kD1 = 0, kD2 = 256, kD3 = 320;
+// D2: per buffer three blocks of PB columns, block j the products with V's piece j
+constexpr unsigned kD2W = 3 * PB;
+constexpr unsigned kD1 = 0, kD2 = 256, kD3 = kD2 + 2 * kD2W;
+static_assert(kD3 + PB <= kTmemCols, "TMEM columns");
 
 // shared-memory map (offsets from the 1024-byte aligned base); the control block first,
 // 256-byte guard bands between the regions (filled with a pattern and checked after every
@@ -371,15 +385,16 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
         bool ok = true;
         if (warp < NEPI) {
             // ---------------- epilogue warp (q, h): rows 32 q .. 32 q + 31 of every tile, columns
-            // 64 h .. 64 h + 63 of the chunk (slots s = 2 h, 2 h + 1), dots t = 16 h .. 16 h + 15
+            // 32 NSW h .. of the chunk (slots s = NSW h ..), dots and final columns t = HT h .. HT h + HT - 1
             const int q = warp & 3, h = warp >> 2;
-            constexpr int HT = PB / 2;
+            constexpr int HT = PB / NH;
+            static_assert(HT == 8 || HT == 16, "TMEM loads of the dots and final columns");
             float acc2[HT];
 #pragma unroll
             for (int t = 0; t < HT; ++t) acc2[t] = 0.f;
             const unsigned lanes = tbase + ((unsigned)(q * 32) << 16);
             unsigned char* myslots = slots + q * NS * kSlotBytes;
-            const int s0 = 2 * h, s1 = 2 * h + 2;
+            const int s0 = NSW * h, s1 = NSW * h + NSW;
             // prefetch the first tile's blocks
             if (lane == 0)
                 for (int s = s0; s < s1; ++s) {
@@ -391,11 +406,27 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
             auto fold_d2 = [&](unsigned g2) -> bool {
                 if (!waitx(&sh->d2_full[g2 & 1], (g2 >> 1) & 1, 2, (int)g2, sh, a)) return false;
                 fence_after();
-                unsigned v0[16];
-                tmem_ld16(lanes + kD2 + (g2 & 1) * PB + h * HT, v0);
-                tmem_wait_ld(v0);
+                // the three blocks (products with V's pieces 0, 1, 2), added smallest first
+                unsigned v0[HT], v1[HT], v2[HT];
+                const unsigned d2a = lanes + kD2 + (g2 & 1) * kD2W + h * HT;
+                if constexpr (HT == 8) {
+                    tmem_ld8(d2a, v0);
+                    tmem_ld8(d2a + PB, v1);
+                    tmem_ld8(d2a + 2 * PB, v2);
+                    tmem_wait_ld8(v0);
+                    tmem_wait_ld8(v1);
+                    tmem_wait_ld8(v2);
+                } else {
+                    tmem_ld16(d2a, v0);
+                    tmem_ld16(d2a + PB, v1);
+                    tmem_ld16(d2a + 2 * PB, v2);
+                    tmem_wait_ld(v0);
+                    reg_fence16(v1);
+                    reg_fence16(v2);
+                }
 #pragma unroll
-                for (int t = 0; t < HT; ++t) acc2[t] += __uint_as_float(v0[t]);
+                for (int t = 0; t < HT; ++t)
+                    acc2[t] += (__uint_as_float(v2[t]) + __uint_as_float(v1[t])) + __uint_as_float(v0[t]);
                 fence_before();
                 mbar_arrive(&sh->d2_empty[g2 & 1]);
                 return true;
@@ -420,22 +451,16 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         break;
                     }
                     if (!upd) continue;
-                    float d[SWC];
-                    {
-                        unsigned u0[16], u1[16];
-                        tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC, u0);
-                        tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC + 16, u1);
+#pragma unroll
+                    for (int hh = 0; hh < SWC; hh += 16) {
+                        unsigned u0[16];
+                        tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC + hh, u0);
                         tmem_wait_ld(u0);
-                        reg_fence16(u1);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) d[j] = __uint_as_float(u0[j]), d[16 + j] = __uint_as_float(u1[j]);
-                    }
-                    float xn[SWC];
-#pragma unroll
-                    for (int j = 0; j < SWC; ++j) {
-                        float* p = slot_at(slot, j, lane);
-                        xn[j] = *p + d[j];
-                        *p = xn[j];
+                        for (int j = 0; j < 16; ++j) {
+                            float* p = slot_at(slot, hh + j, lane);
+                            *p = *p + __uint_as_float(u0[j]);
+                        }
                     }
                     // X_new to global memory from the slot by TMA (rows past nobs and columns past
                     // N lie outside the tensor and are not written)
@@ -446,14 +471,16 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         bulk_commit();
                     }
                     if (writeup && s == 0) {
-                        // pieces of the next panel's U_P (trailing columns 0 .. nbn-1) for this row
+                        // pieces of the next panel's U_P (trailing columns 0 .. nbn-1) for this row,
+                        // read back from the slot (this lane's own row)
                         unsigned char* ub = tile_piece(a.upc, (int64_t)(sp.up_par ^ 1) * a.ntiles + T);
                         const int m = q * 32 + lane;
 #pragma unroll
                         for (int t8 = 0; t8 < 4; ++t8) {
                             float v8[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v8[e] = (t8 * 8 + e < nbn && row < a.nobs) ? xn[t8 * 8 + e] : 0.f;
+                            for (int e = 0; e < 8; ++e)
+                                v8[e] = (t8 * 8 + e < nbn && row < a.nobs) ? *slot_at(slot, t8 * 8 + e, lane) : 0.f;
                             uint4 pc[3];
                             pieces8(v8, pc);
 #pragma unroll
@@ -522,9 +549,14 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         break;
                     }
                     fence_after();
-                    unsigned u0[16];
-                    tmem_ld16(lanes + kD3 + h * HT, u0);
-                    tmem_wait_ld(u0);
+                    unsigned u0[HT];
+                    if constexpr (HT == 8) {
+                        tmem_ld8(lanes + kD3 + h * HT, u0);
+                        tmem_wait_ld8(u0);
+                    } else {
+                        tmem_ld16(lanes + kD3 + h * HT, u0);
+                        tmem_wait_ld(u0);
+                    }
                     if (row < a.nobs) {
 #pragma unroll
                         for (int m = 0; m < HT; ++m)
@@ -535,7 +567,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         // their pieces in MMA1's A order, for the correction sweep
                         unsigned char* fb = tile_piece(a.ufc, (int64_t)(sp.k0 / PB) * a.ntiles + T);
 #pragma unroll
-                        for (int g = 0; g < 2; ++g) {
+                        for (int g = 0; g < HT / 8; ++g) {
                             float v8[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
@@ -546,8 +578,8 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                             pieces8(v8, pc);
 #pragma unroll
                             for (int pq = 0; pq < 3; ++pq)
-                                *reinterpret_cast<uint4*>(fb + pq * kPiece + kmaj_off(q * 32 + lane, 2 * h + g, TR * 32)) =
-                                    pc[pq];
+                                *reinterpret_cast<uint4*>(fb + pq * kPiece +
+                                                          kmaj_off(q * 32 + lane, (HT / 8) * h + g, TR * 32)) = pc[pq];
                         }
                     }
                     fence_before();
@@ -654,8 +686,9 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
             // loaded once MMA2(i) has read V(i), a tile before MMA2(i + 1) needs it).
             if (lane == 0 && dots) {
                 Counters c = cn;
-                const unsigned id2 = instr_desc(TR, PB);
-                const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+                // piece i of the A slice against V's pieces 0 .. 2 - i side by side (N = 32 (3 - i)):
+                // block j of D2 collects the products with V's piece j
+                const unsigned id2[3] = {instr_desc(TR, 3 * PB), instr_desc(TR, 2 * PB), instr_desc(TR, PB)};
                 auto load_vp = [&](int tile) {
                     mbar_expect_tx(&sh->vp_full, kOp3);
                     bulk_load(vp, tile_piece(a.vpc, (int64_t)pv * a.ntiles + T0 + tile), kOp3, &sh->vp_full);
@@ -668,7 +701,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         ok = false;
                         break;
                     }
-                    const unsigned d2 = tbase + kD2 + b * PB;
+                    const unsigned d2 = tbase + kD2 + b * kD2W;
                     for (int q = 0; q < NQ; ++q) {
                         const unsigned sig = 4u * c.g2 + (unsigned)q;
                         if (!waitx(&sh->as_full[q], c.g2 & 1, 10, jt, sh, a)) {
@@ -677,13 +710,13 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                         }
                         fence_after();
                         const unsigned char* asb = as + (sig % kNAs) * kOp3;
-                        const unsigned char* vb = vp + q * (PB * 32 * 2);
+                        const unsigned char* vb = vp + q * (3 * PB * 32 * 2);
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-                            for (int pq = 0; pq < 6; ++pq)
-                                mma_bf16(d2, smem_desc(asb + pa[pq] * kPiece + ks * (CW * 32)),
-                                         smem_desc(vb + pb[pq] * kPiece + ks * (PB * 32)), id2, (q | ks | pq) != 0);
+                            for (int i = 0; i < 3; ++i)
+                                mma_bf16(d2, smem_desc(asb + i * kPiece + ks * (CW * 32)),
+                                         smem_desc(vb + ks * (3 * PB * 32)), id2[i], (q | ks | i) != 0);
                         mma_commit(&sh->as_empty[(q + kNAs) % NQ]);   // the next user of this buffer
                     }
                     if (!ok) break;
@@ -786,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
             mbar_init(&sh->d1_full[q], 1), mbar_init(&sh->d1_empty[q], NEPI * 32);
             mbar_init(&sh->d2_full[q], 1), mbar_init(&sh->d2_empty[q], NEPI * 32);
         }
-        for (int q = 0; q < NQ; ++q) mbar_init(&sh->as_full[q], 64), mbar_init(&sh->as_empty[q], 1);
+        for (int q = 0; q < NQ; ++q) mbar_init(&sh->as_full[q], NH * 32), mbar_init(&sh->as_empty[q], 1);
         mbar_init(&sh->d3_full, 1);
         mbar_init(&sh->d3_empty, NEPI * 32);
         mbar_init(&sh->drained_a, 1);
@@ -982,12 +1015,12 @@ __global__ void __launch_bounds__(256) tc5_step1_kernel(Step1Args a) {
         }
         if (isv) {
             const int pv = col / PB, t = col % PB;
-            unsigned char* dstp = a.vpc + ((int64_t)pv * a.ntiles + T) * (int64_t)kOp3 + (rg >> 2) * (PB * 32 * 2) +
-                                  ((rg & 3) >> 1) * (PB * 32) + (t >> 3) * 256 + (rg & 1) * 128 + (t & 7) * 16;
+            unsigned char* dstp = a.vpc + ((int64_t)pv * a.ntiles + T) * (int64_t)kOp3 + (rg >> 2) * (3 * PB * 32 * 2) +
+                                  ((rg & 3) >> 1) * (3 * PB * 32) + (t >> 3) * 256 + (rg & 1) * 128 + (t & 7) * 16;
             uint4 pc[3];
             pieces8(x8, pc);
 #pragma unroll
-            for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dstp + pq * kPiece) = pc[pq];
+            for (int pq = 0; pq < 3; ++pq) *reinterpret_cast<uint4*>(dstp + pq * (PB * 32)) = pc[pq];
         }
     }
     // panel 0's U_P pieces: thread (row m, 8-wide group t8), U = V / r of the first 32 columns
