@@ -248,7 +248,7 @@ __device__ void check_guards(const unsigned char* sm, Control* ctl) {
 // device array read by enkf_tc5_timers_read.  Entries 0..15: time in the waits of each
 // site (lane 0 of the waiting warp); 16..: phases timed by thread 0 and the MMA thread.
 enum { kTmK = 16, kTmEpi = 17, kTmEnd = 18, kTmRed = 19, kTmFac = 20, kTmAll = 21, kTmChunks = 22, kTmMma = 23,
-       kTmStep1 = 24 };
+       kTmStep1 = 24, kTmXup = 25, kTmConv = 26, kTmMat = 27, kTmFold = 28 };
 #ifdef ENKF_TC5_TIMERS
 constexpr int kOffTimers = kMiscBytes + kGuard;
 constexpr int kNTimers = (kOffSlots - kOffTimers) / 8;
@@ -444,35 +444,53 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 fence_after();
                 // (1) X_new = X + D1 for both slots: written back to the slot (for the transposed
                 // reads below) and stored; the next panel's U_P pieces from chunk 0
-                for (int s = s0; s < s1; ++s) {
-                    unsigned char* slot = myslots + s * kSlotBytes;
+                TC5_T0(tx);
+                static_assert(NSW == 2, "the X update below loads two slots' D1 columns at once");
+                for (int s = s0; s < s1; ++s)
                     if (!waitx(&sh->slot_full[q * NS + s], c.gt & 1, 4, it, sh, a)) {
                         ok = false;
                         break;
                     }
-                    if (!upd) continue;
+                if (!ok) break;
+                unsigned dv0[16], dv1[16], dv2[16], dv3[16];
+                if (upd) {
+                    // every D1 column of this warp's slots in one round trip
+                    const unsigned d1a = lanes + kD1 + (c.g1 & 1) * CW + s0 * SWC;
+                    tmem_ld16(d1a, dv0);
+                    tmem_ld16(d1a + 16, dv1);
+                    tmem_ld16(d1a + SWC, dv2);
+                    tmem_ld16(d1a + SWC + 16, dv3);
+                    tmem_wait_ld(dv0);
+                    reg_fence16(dv1);
+                    reg_fence16(dv2);
+                    reg_fence16(dv3);
+                }
+                if (upd) {
+                    unsigned char* sl0 = myslots + s0 * kSlotBytes;
+                    unsigned char* sl1 = sl0 + kSlotBytes;
 #pragma unroll
-                    for (int hh = 0; hh < SWC; hh += 16) {
-                        unsigned u0[16];
-                        tmem_ld16(lanes + kD1 + (c.g1 & 1) * CW + s * SWC + hh, u0);
-                        tmem_wait_ld(u0);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            float* p = slot_at(slot, hh + j, lane);
-                            *p = *p + __uint_as_float(u0[j]);
-                        }
+                    for (int j = 0; j < 16; ++j) {
+                        float* p0 = slot_at(sl0, j, lane);
+                        float* p1 = slot_at(sl0, 16 + j, lane);
+                        float* p2 = slot_at(sl1, j, lane);
+                        float* p3 = slot_at(sl1, 16 + j, lane);
+                        *p0 = *p0 + __uint_as_float(dv0[j]);
+                        *p1 = *p1 + __uint_as_float(dv1[j]);
+                        *p2 = *p2 + __uint_as_float(dv2[j]);
+                        *p3 = *p3 + __uint_as_float(dv3[j]);
                     }
-                    // X_new to global memory from the slot by TMA (rows past nobs and columns past
+                    // X_new to global memory from the slots by TMA (rows past nobs and columns past
                     // N lie outside the tensor and are not written)
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        tma_store_2d(tm, T * TR + q * 32, acol0 + s * SWC, slot);
+                        for (int s = s0; s < s1; ++s)
+                            tma_store_2d(tm, T * TR + q * 32, acol0 + s * SWC, myslots + s * kSlotBytes);
                         bulk_commit();
                     }
-                    if (writeup && s == 0) {
+                    if (writeup && s0 == 0) {
                         // pieces of the next panel's U_P (trailing columns 0 .. nbn-1) for this row,
-                        // read back from the slot (this lane's own row)
+                        // read back from slot 0 (this lane's own row)
                         unsigned char* ub = tile_piece(a.upc, (int64_t)(sp.up_par ^ 1) * a.ntiles + T);
                         const int m = q * 32 + lane;
 #pragma unroll
@@ -480,7 +498,7 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                             float v8[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e)
-                                v8[e] = (t8 * 8 + e < nbn && row < a.nobs) ? *slot_at(slot, t8 * 8 + e, lane) : 0.f;
+                                v8[e] = (t8 * 8 + e < nbn && row < a.nobs) ? *slot_at(sl0, t8 * 8 + e, lane) : 0.f;
                             uint4 pc[3];
                             pieces8(v8, pc);
 #pragma unroll
@@ -490,6 +508,9 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                     }
                 }
                 if (!ok) break;
+#ifdef ENKF_TC5_TIMERS
+                if (tid == 0) TC5_ADD(sm, kTmXup, tx);
+#endif
                 if (upd) {
                     // D1 has been read: MMA1 of tile it + 2 may overwrite it
                     fence_before();
@@ -509,10 +530,11 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                 // (3) the slots' 32 columns x this quarter's 32 rows -> pieces of MMA2's A operand
                 // (M = chunk column, K = row): lane = column, four 8-row groups; then the slot
                 // takes the next tile's block
+                TC5_T0(tcv);
+                if (dots) __syncwarp();       // the other lanes' rows of the slots are written
                 for (int s = s0; s < s1; ++s) {
                     unsigned char* slot = myslots + s * kSlotBytes;
                     if (dots) {
-                        __syncwarp();
                         const int cm = s * SWC + lane;
 #pragma unroll
                         for (int g4 = 0; g4 < 4; ++g4) {
@@ -532,15 +554,23 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                                 *reinterpret_cast<uint4*>(asb + pq * kPiece + kmaj_off(cm, g4, CW * 32)) = pc[pq];
                         }
                     }
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0 && it + 1 < ntl) {
-                        if (upd) bulk_wait_read0();       // the slot's store has read it
+                }
+                // the pieces are read by MMA2 and the slots rewritten by TMA (async proxy)
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0 && it + 1 < ntl) {
+                    if (upd) bulk_wait_read0();       // the slots' stores have read them
+                    for (int s = s0; s < s1; ++s) {
                         mbar_expect_tx(&sh->slot_full[q * NS + s], kSlotBytes);
-                        tma_load_2d(slot, tm, (T + 1) * TR + q * 32, acol0 + s * SWC, &sh->slot_full[q * NS + s]);
+                        tma_load_2d(myslots + s * kSlotBytes, tm, (T + 1) * TR + q * 32, acol0 + s * SWC,
+                                    &sh->slot_full[q * NS + s]);
                     }
                 }
                 if (dots) mbar_arrive(&sh->as_full[q]);
+#ifdef ENKF_TC5_TIMERS
+                if (tid == 0) TC5_ADD(sm, kTmConv, tcv);
+#endif
+                TC5_T0(tmt);
                 if (lane == 0) ((volatile int*)sh->prog)[warp] = 16 * (int)c.gt + 2;
                 if (mat) {
                     // the panel's final columns u_{k0+m} = U_P beta_m for these rows
@@ -585,11 +615,18 @@ __device__ bool sweep_tc5(const Tc5Args& a, const CUtensorMap* tmU, const CUtens
                     fence_before();
                     mbar_arrive(&sh->d3_empty);
                 }
+#ifdef ENKF_TC5_TIMERS
+                if (tid == 0) TC5_ADD(sm, kTmMat, tmt);
+#endif
+                TC5_T0(tfd);
                 if (lane == 0) ((volatile int*)sh->prog)[warp] = 16 * (int)c.gt + 3;
                 if (dots && it > 0 && !fold_d2(c.g2 - 1)) {
                     ok = false;
                     break;
                 }
+#ifdef ENKF_TC5_TIMERS
+                if (tid == 0) TC5_ADD(sm, kTmFold, tfd);
+#endif
                 c.gt++;
                 if (upd) c.g1++;
                 if (dots) c.g2++;
