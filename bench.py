@@ -573,7 +573,20 @@ def run_ours(args):
     inner = ("panel_kernel", "correction_kernel")      # kernels timed inside other phases
     total_ms = sum(v[0] for k, v in phases.items() if k not in inner)
     ms_step = t_max / args.steps
-    launches = 1 + 1 + (14 if refine else 5)
+    # library kernels per step: the prep; the solve (Step 1 and the panel kernel on the tcgen05
+    # path); without refinement the Gram, the assembly of M, the split images of M and X_A; with
+    # it the Gram of V and U, P, the residual (prep, -P, images, X_A-type product), the
+    # correction, V^T delta (the identity on the tcgen05 path, a Gram elsewhere), the update of
+    # Z and M, and X_A (an exact Gram of V and Z1 for FP16 instead of P)
+    tc5_path = args.mode == "bf16x3" and args.panel_b == 32
+    solve_launches = 2 if tc5_path else 1
+    if not refine:
+        after = 5
+    elif args.mode == "fp16":
+        after = 14
+    else:
+        after = 12 if tc5_path else 13
+    launches = 1 + solve_launches + after
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -58,7 +58,7 @@ struct enkf_ism_plan_s {
     int64_t ldu, ldzw;
     // workspace layout (byte offsets)
     size_t off_ctl, off_U, off_Z, off_part, off_coefg, off_C, off_gamma, off_Qpart, off_Q, off_M, off_M64, off_Msplit,
-        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, off_vpc, off_upc, off_ufc, off_wfin, total;
+        off_delta, off_P, off_Md, off_rnorm, off_vp, off_up, off_vpc, off_upc, off_ufc, off_wfin, off_Cd, total;
     int64_t ldp;              // row pitch of the 16-bit operand pieces (tensor-core panel modes)
     bool refine;
     // latched status of the previous call
@@ -204,6 +204,7 @@ enkf_status enkf_ism_plan(enkf_ism_plan_t* out, int64_t nstate, int64_t nobs, in
         // the tensor-core solve's stored factors for its correction sweep
         p->off_ufc = o; o = align256(o + (p->tc5 ? tc5_vpc_bytes(nobs, nens) : 0));
         p->off_wfin = o; o = align256(o + (p->tc5 ? tc5_wfin_bytes(nens) : 0));
+        p->off_Cd = o; o = align256(o + (p->tc5 ? sizeof(double) * N * N : 0));
     }
     p->total = o;
     e = cudaMallocHost(&p->h_status, sizeof(int));   // pinned host word, not device memory
@@ -463,18 +464,24 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
             CU(assemble_M(p->fp64, p->nens, Q, a.C, a.gamma, Mp, M64, s), "assemble_M launch");
             prof_end(p, slot, s);
         } else {
-            // One step of iterative refinement: P = V^T Z (compensated Gram), the scaled residual
-            // R^-1 (D - r o Z - V P), the stored factors (final U columns, gamma' and L from
-            // one Gram Q = V^T U) applied to it giving delta, then Z += delta and
-            // M = (P + V^T delta) / sqrt(N - 1).
+            // One step of iterative refinement: P = V^T Z1 from the coefficient identity of the
+            // solve, the scaled residual R^-1 (D - r o Z1 - V P), the solve's stored factors applied
+            // to it giving delta, then Z = Z1 + delta and M = (P + V^T delta) / sqrt(N - 1).  An
+            // error e in P enters M only as (I + V^T R^-1 V)^-1 e (~e / gamma): the correction
+            // takes up V e in the residual.
             slot = prof_begin(p, 5, s);
             double* P = (double*)(ws + p->off_P);
             double* Pd = (double*)(ws + p->off_Md);
             double* part = (double*)(ws + p->off_Qpart);
             float* delta = (float*)(ws + p->off_delta);
-            {
-                // fixed-point digits on the tensor cores when V and Z are TMA-aligned, else
-                // compensated FP32 sums on CUDA cores
+            // P from the identity needs the solve's own e = V^T Z1 - P well below gamma times the
+            // target: true for the FP32-class and split-BF16 solves (e ~ u gamma |M| with u <= 2^-17),
+            // not for the FP16 solve (u = 2^-11), which takes V^T Z1 summed exactly instead
+            const bool p_identity = p->mode != ENKF_PANEL_FP16;
+            if (info || !p_identity) {
+                // V^T Z1 summed exactly, and (diagnostic) the true relative residual of Z1
+                // (fixed-point digits on the tensor cores when V and Z are TMA-aligned, else
+                // compensated FP32 sums on CUDA cores)
                 cudaError_t eg = gram_exact(p->nobs, p->nens, (const float*)V, ldv, (const float*)Zp, ldzp, part,
                                             p->nsplit, P, ctl, a.timeout_ns, s);
                 if (eg == cudaErrorNotSupported) {
@@ -483,22 +490,41 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                                    P, s);
                 }
                 CU(eg, "refine Gram V^T Z");
+                CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
+                                   (const float*)Zp, ldzp, P, (float*)Mp, ws + p->off_Msplit, delta, p->ldzw, ctl,
+                                   a.timeout_ns, s),
+                   "refine residual (exact V^T Z1)");
+                if (info)
+                    CU(refine_resid_norm(p->nobs, p->nens, delta, p->ldzw, (const float*)r, (const float*)D, ldd,
+                                         (double*)(ws + p->off_rnorm), (double*)(ws + p->off_rnorm) + 1024, s),
+                       "refine residual norm");
             }
-            // Mp (M's output, written last by refine_apply) holds -P in FP32 until then
-            CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
-                               (const float*)Zp, ldzp, P, (float*)Mp, ws + p->off_Msplit, delta, p->ldzw, ctl,
-                               a.timeout_ns, s),
-               "refine residual");
-            if (info)
-                CU(refine_resid_norm(p->nobs, p->nens, delta, p->ldzw, (const float*)r, (const float*)D, ldd,
-                                     (double*)(ws + p->off_rnorm), (double*)(ws + p->off_rnorm) + 1024, s),
-                   "refine residual norm");
+            // Q = V^T U of the final columns (the full Gram where the CUDA-core correction needs
+            // its diagonal and lower part too), then P = (I - triu(Q,1)) diag(1/gamma) C
+            const bool qfull = !solved_tc5;
+            if (qfull)
+                CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
+                   "refine Gram V^T U");
+            else
+                CU(gram_upper(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns,
+                              s),
+                   "refine Gram V^T U (upper)");
+            if (p_identity) {
+                CU(assemble_P(p->nens, Q, a.C, a.gamma, P, s), "refine P");
+                // Mp (M's output, written last by refine_apply) holds -P in FP32 until then
+                CU(refine_residual(p->nobs, p->nens, (const float*)r, (const float*)V, ldv, (const float*)D, ldd,
+                                   (const float*)Zp, ldzp, P, (float*)Mp, ws + p->off_Msplit, delta, p->ldzw, ctl,
+                                   a.timeout_ns, s),
+                   "refine residual");
+            }
             PanelArgs ra = panel_args;
             ra.Z = delta;
             ra.ldz = p->ldzw;
             CU(cudaMemsetAsync(&ctl->barrier, 0, sizeof(unsigned), s), "barrier reset");
             cudaError_t ec = cudaErrorNotSupported;
+            double* Cd = (double*)(ws + p->off_Cd);
             if (solved_tc5) {
+                ra.C = Cd;
                 // the tensor-core solve's own stored factors (final-column pieces, per-panel
                 // diag(1/gamma) (I + L)^-1)
                 const int k7 = prof_begin(p, 7, s);
@@ -508,8 +534,10 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                 else CU(ec, "stored-factor correction (tensor cores)");
             }
             if (ec == cudaErrorNotSupported) {
-                CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns, s),
-                   "refine Gram V^T U");
+                if (!qfull)
+                    CU(gram_full(false, p->nobs, p->nens, V, ldv, a.U, p->ldu, part, p->nsplit, Q, ctl, a.timeout_ns,
+                                 s),
+                       "refine Gram V^T U");
                 ra.Qg = Q;
                 ra.refine = 1;
                 ra.vec_ok = panel_args.vec_ok && (p->ldzw % 4 == 0);
@@ -517,8 +545,13 @@ enkf_status enkf_ism_analysis(enkf_ism_plan_t p, const void* r, const void* V, i
                 CU(panel_launch(p->P, ra, s), "stored-factor correction");
                 prof_end(p, k7, s);
             }
-            CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, ctl, a.timeout_ns, s),
-               "refine Gram V^T delta");
+            if (ec == cudaSuccess)
+                // V^T delta from the correction's own per-level coefficients (the identity above)
+                CU(assemble_P(p->nens, Q, Cd, a.gamma, Pd, s), "refine V^T delta");
+            else
+                CU(gram_full(false, p->nobs, p->nens, V, ldv, delta, p->ldzw, part, p->nsplit, Pd, ctl, a.timeout_ns,
+                             s),
+                   "refine Gram V^T delta");
             CU(refine_apply(p->nobs, p->nens, (float*)Zp, ldzp, delta, p->ldzw, P, Pd, M64, (float*)Mp, s),
                "refine apply");
             prof_end(p, slot, s);

@@ -151,6 +151,17 @@ __global__ void assemble_M_kernel(int n, const double* __restrict__ Q, const dou
     if (M64) M64[e] = s;
 }
 
+// P = V^T Z by the same identity, unscaled and row-major (P[k n + i] = v_k^T z_i).
+__global__ void assemble_P_kernel(int n, const double* __restrict__ Q, const double* __restrict__ C,
+                                  const double* __restrict__ gamma, double* __restrict__ P) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * n) return;
+    const int k = (int)(e / n), i = (int)(e % n);
+    double s = C[(int64_t)k * n + i] / gamma[k];
+    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] / gamma[m]);
+    P[e] = s;
+}
+
 // ---------------------------------------------------------------------------
 // XA = XB + dXB * M.  CTA tile 128 rows x 64 columns, 256 threads; lane -> 4 rows
 // (lane + 32 r), warp -> 8 columns.  The 64 needed columns of M sit in smem for
@@ -279,6 +290,13 @@ cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C
         assemble_M_kernel<double><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (double*)M, M64);
     else
         assemble_M_kernel<float><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (float*)M, M64);
+    return cudaGetLastError();
+}
+
+cudaError_t assemble_P(int32_t nens, const double* Q, const double* C, const double* gamma, double* P,
+                       cudaStream_t s) {
+    const int64_t nn = (int64_t)nens * nens;
+    assemble_P_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(nens, Q, C, gamma, P);
     return cudaGetLastError();
 }
 

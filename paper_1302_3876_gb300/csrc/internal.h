@@ -189,6 +189,10 @@ cudaError_t refine_apply(int64_t nobs, int32_t n, float* Z, int64_t ldz, const f
 cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C, const double* gamma,
                        void* M, double* M64, cudaStream_t s);
 
+// P = (I - triu(Q,1)) diag(1/gamma) C = V^T Z unscaled, row-major P[k n + i].
+cudaError_t assemble_P(int32_t nens, const double* Q, const double* C, const double* gamma, double* P,
+                       cudaStream_t s);
+
 // XA = XB + dXB * M  (nstate x nens, K = nens); XA may alias XB.
 cudaError_t xa_update(bool fp64, int64_t nstate, int32_t nens, const void* XB, int64_t ldb,
                       const void* dXB, int64_t ldx, const void* M, void* XA, int64_t lda, cudaStream_t s);

@@ -905,6 +905,20 @@ __global__ void __launch_bounds__(kThreads, 1) ism_panel_tc05_kernel(const __gri
         if (a.refine) {
             // the panel's stored factor: K = -diag(1/gamma) (I + L)^-1 A applied to the final columns
             for (int e = tid; e < PB * PB; e += kThreads) fv.W[e] = __ldcg(&a.wfin[(int64_t)pidx * PB * PB + e]);
+            if (a.C) {
+                // the per-level coefficients c = (I + L)^-1 a of the corrected columns (one warp per
+                // column, CTAs round-robin), so that V^T of the result follows from the identity
+                // V^T x = (I - triu(Q,1)) diag(1/gamma) C without another pass over the rows
+                __syncthreads();
+                const int lane = tid & 31;
+                for (int i = blockIdx.x * (kThreads / 32) + warp; i < N; i += gridDim.x * (kThreads / 32))
+                    if (lane < bp) {
+                        double v = 0.0;
+                        for (int u = 0; u < bp; ++u)
+                            v = fma((double)fv.W[lane * PB + u], __ldcg(&a.coefg[(int64_t)u * N + i]), v);
+                        a.C[(int64_t)(k0 + lane) * N + i] = v * __ldcg(&a.gamma[k0 + lane]);
+                    }
+            }
             nb = (N - k1) < b ? (N - k1) : b;
             SweepSpec s2 = {k0, bp, N, k1, nb, 0, N, 0, 0, tile_piece(a.ufc, (int64_t)pidx * a.ntiles)};
             ok = sweep_tc5(a, &tmU, &tmZ, sm, sh, tbase, s2, cn);
@@ -1187,6 +1201,8 @@ cudaError_t tc5_solve(const Tc5Launch& L, const PanelArgs& p, void* vpc, void* u
 // wfin) applied to p.Z, which holds R^-1 times a right-hand side: p.Z <- W^-1 R p.Z, the
 // levels of Step 2 in panel form with no U columns left to update.  p.U, p.coefg, p.part
 // and p.ctl as for the solve (U is not written); the grid-barrier word must be zero.
+// p.gamma: the solve's gamma; p.C (nullable, N x N doubles): receives the per-level
+// coefficients c_k = v_k^T x^(k-1) of the corrected columns.
 cudaError_t tc5_correct(const Tc5Launch& L, const PanelArgs& p, const void* vpc, const void* ufc,
                         const float* wfin, cudaStream_t s) {
     CUtensorMap tmU, tmZ;
@@ -1216,6 +1232,8 @@ cudaError_t tc5_correct(const Tc5Launch& L, const PanelArgs& p, const void* vpc,
     a.ufc = const_cast<unsigned char*>(static_cast<const unsigned char*>(ufc));
     a.wfin = const_cast<float*>(wfin);
     a.refine = 1;
+    a.C = p.C;              // nullable: the per-level coefficients of the corrected columns
+    a.gamma = p.gamma;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(ism_panel_tc05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem)) !=
         cudaSuccess)
