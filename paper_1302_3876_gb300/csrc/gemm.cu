@@ -141,11 +141,14 @@ __global__ void gram_reduce_kernel(int n, int nsplit, const double* __restrict__
 template <typename T>
 __global__ void assemble_M_kernel(int n, const double* __restrict__ Q, const double* __restrict__ C,
                                   const double* __restrict__ gamma, T* __restrict__ M, double* __restrict__ M64) {
+    extern __shared__ double ginv[];     // 1 / gamma_m, one division per level per CTA
+    for (int m = threadIdx.x; m < n; m += blockDim.x) ginv[m] = 1.0 / gamma[m];
+    __syncthreads();
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)n * n) return;
     const int k = (int)(e % n), i = (int)(e / n);
-    double s = C[(int64_t)k * n + i] / gamma[k];
-    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] / gamma[m]);
+    double s = C[(int64_t)k * n + i] * ginv[k];
+    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] * ginv[m]);
     s *= 1.0 / sqrt((double)(n - 1));
     if (M) M[e] = (T)s;
     if (M64) M64[e] = s;
@@ -154,11 +157,14 @@ __global__ void assemble_M_kernel(int n, const double* __restrict__ Q, const dou
 // P = V^T Z by the same identity, unscaled and row-major (P[k n + i] = v_k^T z_i).
 __global__ void assemble_P_kernel(int n, const double* __restrict__ Q, const double* __restrict__ C,
                                   const double* __restrict__ gamma, double* __restrict__ P) {
+    extern __shared__ double ginv[];     // 1 / gamma_m, one division per level per CTA
+    for (int m = threadIdx.x; m < n; m += blockDim.x) ginv[m] = 1.0 / gamma[m];
+    __syncthreads();
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)n * n) return;
     const int k = (int)(e / n), i = (int)(e % n);
-    double s = C[(int64_t)k * n + i] / gamma[k];
-    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] / gamma[m]);
+    double s = C[(int64_t)k * n + i] * ginv[k];
+    for (int m = k + 1; m < n; ++m) s -= Q[(int64_t)k * n + m] * (C[(int64_t)m * n + i] * ginv[m]);
     P[e] = s;
 }
 
@@ -287,16 +293,16 @@ cudaError_t assemble_M(bool fp64, int32_t nens, const double* Q, const double* C
     const int64_t nn = (int64_t)nens * nens;
     const int blocks = (int)((nn + 255) / 256);
     if (fp64)
-        assemble_M_kernel<double><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (double*)M, M64);
+        assemble_M_kernel<double><<<blocks, 256, sizeof(double) * nens, s>>>(nens, Q, C, gamma, (double*)M, M64);
     else
-        assemble_M_kernel<float><<<blocks, 256, 0, s>>>(nens, Q, C, gamma, (float*)M, M64);
+        assemble_M_kernel<float><<<blocks, 256, sizeof(double) * nens, s>>>(nens, Q, C, gamma, (float*)M, M64);
     return cudaGetLastError();
 }
 
 cudaError_t assemble_P(int32_t nens, const double* Q, const double* C, const double* gamma, double* P,
                        cudaStream_t s) {
     const int64_t nn = (int64_t)nens * nens;
-    assemble_P_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(nens, Q, C, gamma, P);
+    assemble_P_kernel<<<(int)((nn + 255) / 256), 256, sizeof(double) * nens, s>>>(nens, Q, C, gamma, P);
     return cudaGetLastError();
 }
 
