@@ -82,13 +82,14 @@ typedef enum {
 
 /* Plan flags. */
 #define ENKF_FLAG_REFINE        0x1u  /* panel modes: one step of iterative refinement of Z and M:
-                                         the residual R^{-1}(D - (R + V V^T) Z) with V^T Z and the
-                                         N-term sums formed from exact products and compensated sums,
-                                         corrected by the stored factors (final U columns, gamma and L
-                                         from one Gram V^T U); M = V^T (Z + delta) / sqrt(Nens - 1).
-                                         One step contracts the error by about u * gamma_max (u the
-                                         operand precision): effective for PANEL_FP32 and PANEL_BF16,
-                                         not for PANEL_FP16 once gamma_max approaches 1/u = 2^11 */
+                                         the residual R^{-1}(D - r o Z - V P), P = V^T Z taken from
+                                         the solve's own per-level coefficients (summed exactly from
+                                         the columns for PANEL_FP16), corrected by the solve's stored
+                                         panel factors; M = (P + V^T delta) / sqrt(Nens - 1).  One step
+                                         contracts the error by about u * gamma_max (u the operand
+                                         precision): effective for PANEL_FP32, PANEL_BF16X3 and
+                                         PANEL_BF16, not for PANEL_FP16 once gamma_max approaches
+                                         1/u = 2^11 */
 #define ENKF_FLAG_NO_CHECKS     0x2u  /* skip the device-side gamma / finiteness checks */
 #define ENKF_FLAG_TEST_TIMEOUT  0x4u  /* test only: one CTA skips its first grid-barrier arrival,
                                          so the others' bounded wait expires (ENKF_ERR_TIMEOUT) */
