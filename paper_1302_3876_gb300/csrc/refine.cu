@@ -24,6 +24,9 @@
 // V^T delta needs no compensation either: delta is the small correction, so the plain
 // Gram's relative error is scaled by |delta|/|Z|.
 #include <math.h>
+#include <stdint.h>
+
+#include <initializer_list>
 
 #include "internal.h"
 
@@ -117,15 +120,58 @@ __global__ void gram_comp_reduce_kernel(int n, int nsplit, const double* __restr
     }
 }
 
+// The element-wise passes over Nobs x N column blocks below take one member column per
+// blockIdx.y (stepping by gridDim.y) and the rows of that column grid-stride along x, as
+// float4 accesses when Nobs, every leading dimension and every base are multiples of 4
+// floats (16 bytes), else one element per thread.  No per-element index division.
+inline bool vec4_ok(int64_t nobs, std::initializer_list<const void*> ptrs, std::initializer_list<int64_t> lds) {
+    if (nobs % 4 != 0) return false;
+    for (const void* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 16 != 0) return false;
+    for (int64_t ld : lds)
+        if (ld % 4 != 0) return false;
+    return true;
+}
+
+// Grid of the element-wise passes: about 16 CTAs of 256 threads per SM in all, no more
+// x-blocks than a column has 256-unit rows.
+inline dim3 ew_grid(int64_t nobs, int n, bool vec) {
+    const int64_t units = vec ? nobs / 4 : nobs;
+    const int gy = n < 65535 ? (n > 0 ? n : 1) : 65535;
+    int64_t gx = (152 * 16 + gy - 1) / gy;
+    const int64_t need = (units + 255) / 256;
+    if (gx > need) gx = need;
+    if (gx < 1) gx = 1;
+    return dim3((unsigned)gx, (unsigned)gy);
+}
+
 // T = D - r o Z1, one FP32 fused multiply-add per element (one rounding).
-__global__ void residual_prep_kernel(int64_t nobs, int n, const float* __restrict__ r, const float* __restrict__ D,
-                                     int64_t ldd, const float* __restrict__ Z, int64_t ldz, float* __restrict__ out,
-                                     int64_t ldo) {
-    const int64_t total = nobs * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / nobs);
-        const int64_t j = q % nobs;
-        out[(int64_t)i * ldo + j] = __fmaf_rn(-r[j], Z[(int64_t)i * ldz + j], D[(int64_t)i * ldd + j]);
+template <bool VEC>
+__global__ void __launch_bounds__(256) residual_prep_kernel(int64_t nobs, int n, const float* __restrict__ r,
+                                                            const float* __restrict__ D, int64_t ldd,
+                                                            const float* __restrict__ Z, int64_t ldz,
+                                                            float* __restrict__ out, int64_t ldo) {
+    const int64_t units = VEC ? nobs / 4 : nobs;
+    const int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, qs = (int64_t)gridDim.x * blockDim.x;
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
+        const float* d = D + (int64_t)i * ldd;
+        const float* z = Z + (int64_t)i * ldz;
+        float* o = out + (int64_t)i * ldo;
+        for (int64_t q = q0; q < units; q += qs) {
+            if (VEC) {
+                const float4 rv = __ldg(reinterpret_cast<const float4*>(r) + q);
+                const float4 dv = __ldcs(reinterpret_cast<const float4*>(d) + q);
+                const float4 zv = __ldcs(reinterpret_cast<const float4*>(z) + q);
+                float4 ov;
+                ov.x = __fmaf_rn(-rv.x, zv.x, dv.x);
+                ov.y = __fmaf_rn(-rv.y, zv.y, dv.y);
+                ov.z = __fmaf_rn(-rv.z, zv.z, dv.z);
+                ov.w = __fmaf_rn(-rv.w, zv.w, dv.w);
+                reinterpret_cast<float4*>(o)[q] = ov;
+            } else {
+                o[q] = __fmaf_rn(-r[q], z[q], d[q]);
+            }
+        }
     }
 }
 
@@ -178,18 +224,35 @@ __global__ void resid_norm_final_kernel(const double* __restrict__ part, double*
 }
 
 // Z += delta;  M[k + i n] = (P[k][i] + Pd[k][i]) / sqrt(n - 1)  (P, Pd row-major).
-__global__ void refine_apply_kernel(int64_t nobs, int n, float* Z, int64_t ldz, const float* __restrict__ delta,
-                                    int64_t ldd, const double* __restrict__ P, const double* __restrict__ Pd,
-                                    double* M64, float* M) {
-    const int64_t total = nobs * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q / nobs);
-        const int64_t j = q % nobs;
-        Z[(int64_t)i * ldz + j] += delta[(int64_t)i * ldd + j];
+template <bool VEC>
+__global__ void __launch_bounds__(256) refine_apply_kernel(int64_t nobs, int n, float* Z, int64_t ldz,
+                                                           const float* __restrict__ delta, int64_t ldd,
+                                                           const double* __restrict__ P, const double* __restrict__ Pd,
+                                                           double* M64, float* M) {
+    const int64_t units = VEC ? nobs / 4 : nobs;
+    const int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, qs = (int64_t)gridDim.x * blockDim.x;
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
+        float* z = Z + (int64_t)i * ldz;
+        const float* dl = delta + (int64_t)i * ldd;
+        for (int64_t q = q0; q < units; q += qs) {
+            if (VEC) {
+                float4 zv = __ldcs(reinterpret_cast<const float4*>(z) + q);
+                const float4 dv = __ldcs(reinterpret_cast<const float4*>(dl) + q);
+                zv.x += dv.x;
+                zv.y += dv.y;
+                zv.z += dv.z;
+                zv.w += dv.w;
+                reinterpret_cast<float4*>(z)[q] = zv;
+            } else {
+                z[q] += dl[q];
+            }
+        }
     }
     const int64_t nn = (int64_t)n * n;
     const double scale = 1.0 / sqrt((double)(n - 1));
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nthreads = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+    for (int64_t q = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; q < nn;
+         q += nthreads) {
         const int k = (int)(q % n), i = (int)(q / n);
         const double v = (P[(int64_t)k * n + i] + Pd[(int64_t)k * n + i]) * scale;
         if (M64) M64[q] = v;
@@ -218,10 +281,12 @@ cudaError_t gram_comp(int64_t nrows, int32_t n, const float* A, int64_t lda, con
 cudaError_t refine_residual(int64_t nobs, int32_t n, const float* r, const float* V, int64_t ldv, const float* D,
                             int64_t ldd, const float* Z, int64_t ldz, const double* P, float* Mneg, void* msplit,
                             float* delta, int64_t ldo, Control* ctl, uint64_t timeout_ns, cudaStream_t s) {
-    int64_t blocks = (nobs * n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (blocks < 1) blocks = 1;
-    residual_prep_kernel<<<(int)blocks, 256, 0, s>>>(nobs, n, r, D, ldd, Z, ldz, delta, ldo);
+    const bool vec = vec4_ok(nobs, {r, D, Z, delta}, {ldd, ldz, ldo});
+    const dim3 grid = ew_grid(nobs, n, vec);
+    if (vec)
+        residual_prep_kernel<true><<<grid, 256, 0, s>>>(nobs, n, r, D, ldd, Z, ldz, delta, ldo);
+    else
+        residual_prep_kernel<false><<<grid, 256, 0, s>>>(nobs, n, r, D, ldd, Z, ldz, delta, ldo);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t nn = (int64_t)n * n;
@@ -242,10 +307,12 @@ cudaError_t refine_resid_norm(int64_t nobs, int32_t n, const float* delta, int64
 
 cudaError_t refine_apply(int64_t nobs, int32_t n, float* Z, int64_t ldz, const float* delta, int64_t ldd,
                          const double* P, const double* Pd, double* M64, float* M, cudaStream_t s) {
-    int64_t blocks = (nobs * n + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (blocks < 1) blocks = 1;
-    refine_apply_kernel<<<(int)blocks, 256, 0, s>>>(nobs, n, Z, ldz, delta, ldd, P, Pd, M64, M);
+    const bool vec = vec4_ok(nobs, {Z, delta}, {ldz, ldd});
+    const dim3 grid = ew_grid(nobs, n, vec);
+    if (vec)
+        refine_apply_kernel<true><<<grid, 256, 0, s>>>(nobs, n, Z, ldz, delta, ldd, P, Pd, M64, M);
+    else
+        refine_apply_kernel<false><<<grid, 256, 0, s>>>(nobs, n, Z, ldz, delta, ldd, P, Pd, M64, M);
     return cudaGetLastError();
 }
 
