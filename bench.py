@@ -921,8 +921,9 @@ def run_next_rows(args):
     inflation fused into the prep (Nstate 2^21, every 4th variable observed, 128 members, FP32), partial
     localization (the Lorenz-96 cycle size Nstate 4096 / Nobs 2048 / 256 members with the paper's weights
     exp(-d / Nstate), and a 64-point cut-off at Nstate 2^21 / Nobs 2^19 / 128 members), the block-diagonal
-    R path (32 x 32 blocks at Nobs 2^19, 128 members: whitening, analysis with r = 1, unwhitening), and the
-    Lorenz-96 filter with inflation and localization against the unlocalized filter (analysis RMSE)."""
+    R path (32 x 32 blocks at Nobs 2^19, 128 members: whitening, analysis with r = 1, unwhitening), the
+    pivoted solve, one rank's share of the row-sharded analysis (the panel workload split over 8 ranks),
+    and the Lorenz-96 filter with inflation and localization against the unlocalized filter (analysis RMSE)."""
     import torch
     import synth
     from paper_1302_3876_gb300 import cycle as C
@@ -1054,6 +1055,38 @@ def run_next_rows(args):
             del r, V, D, Z, M, ws
         out["pivoted_solve"] = {"config": f"Nobs={nobs} Nens={nens}", "paths": res}
 
+    if part in ("all", "rows"):
+        # N-1: one rank's share of the row-sharded analysis, the panel workload split over 8 ranks by
+        # observation rows (Nobs 2^17, Nstate 2^19, 256 members, FP32; inputs larger than L2).  One GPU
+        # holds one rank here, so the exchange is the identity: the timed region is the rank's own work
+        # (Step 1, one level pass per level, the Gram of the final columns, M, X_A and the status read),
+        # without the collectives (2N doubles per level and one N x N Gram across the ranks).
+        from paper_1302_3876_gb300 import sharded
+        nobs, nens = (1 << 20) // 8, 256
+        nstate = nobs * STRIDE
+        r = 0.5 + torch.rand(nobs, device=dev, generator=gen)
+        V = torch.randn(nens, nobs, device=dev, generator=gen) / math.sqrt(nens - 1)
+        D = torch.randn(nens, nobs, device=dev, generator=gen)
+        dX = torch.randn(nens, nstate, device=dev, generator=gen)
+        XB = dX + 8.0
+        XA = torch.empty_like(XB)
+        fn = lambda: sharded.sharded_analysis(r, V, D, dX, XB, XA, lambda t: None)  # noqa: E731
+        for _ in range(args.warmup):
+            fn()
+        ms = _events_ms(fn, min(k, 10))
+        w = 4
+        # Step 1 reads r, D and V and writes Z and U (and reads v_0); level k reads and writes the N
+        # columns of Z and the N - k - 1 active columns of U, and reads u_k and v_{k+1}
+        lvl = w * nobs * (4 * nens + 2) + sum(w * nobs * (2 * (2 * nens - kk - 1) + (2 if kk + 1 < nens else 1))
+                                              for kk in range(nens))
+        nbytes = lvl + 2 * w * nobs * nens + 3 * w * nstate * nens     # + the Gram's V and U, X_A's three arrays
+        out["rows_block"] = {
+            "config": f"one rank of 8: Nobs={nobs} Nstate={nstate} Nens={nens} FP32, exchange not timed",
+            "ms_per_analysis": ms, "launches": 2 * nens + 5, "level_pass_bytes": lvl,
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "bytes": nbytes, "peak_source": hbm_src}}
+        del r, V, D, dX, XB, XA
+
     if part in ("all", "cycle"):
         # partial localization leaves (R + V V^T)^{-1} unlocalized: with short correlation lengths the
         # cycle diverges (the analysis then reports ENKF_ERR_NUMERIC), which is recorded, not raised
@@ -1099,7 +1132,8 @@ def main():
                          "the one that meets 1e-5 on Z, M, X_A and the increment)")
     ap.add_argument("--workload", choices=["panel_single", "large_single", "panel_paths", "lorenz_small",
                                            "batch_local", "lorenz_cycle", "next_rows"], default="panel_single")
-    ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "pivot", "cycle"], default="all",
+    ap.add_argument("--next-part", choices=["all", "inflate", "localize", "rblock", "pivot", "rows", "cycle"],
+                    default="all",
                     help="next_rows workload: run one part only")
     ap.add_argument("--cycles", type=int, default=200, help="next_rows workload: assimilation cycles per filter")
     ap.add_argument("--train-cycles", type=int, default=60)
