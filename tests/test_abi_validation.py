@@ -1,7 +1,8 @@
 """Host-side argument checks of the entry points beside the analysis (inflation, partial
-localization, block-diagonal R, pivoted solve), run on the CPU: every call here is rejected by
-the library's validation before it touches the GPU, so placeholder device addresses (never
-dereferenced) stand in for arrays.  Also the workspace sizing of the pivoted solve."""
+localization, block-diagonal R, pivoted solve, the row-sharded analysis), run on the CPU: every
+call here is rejected by the library's validation before it touches the GPU, so placeholder
+device addresses (never dereferenced) stand in for arrays.  Also the workspace sizing of the
+pivoted solve and of the row-sharded analysis."""
 import ctypes
 import math
 
@@ -123,3 +124,66 @@ def test_pivoted_solve_rejects_bad_arguments(lib):
     assert _piv(lib, ws_bytes=1024) == WS
     assert _piv(lib, ws=ctypes.c_void_p(0x600000010)) == WS     # not 256-byte aligned
     assert _piv(lib, M=ctypes.c_void_p(0x500000002)) == ARG
+
+
+# ---------------------------------------------------------------------------
+# Row-sharded entry points (enkf_rows_*): sizing and the host-side checks.
+
+
+def _rows_ws(lib, nobs, nens):
+    b = ctypes.c_size_t(0)
+    st = lib.enkf_rows_workspace(nobs, nens, ctypes.byref(b))
+    return st, b.value
+
+
+def test_rows_workspace_sizes(lib):
+    st, small = _rows_ws(lib, 1000, 16)
+    assert st == enkf.ENKF_OK and small > 0
+    # per-CTA partial dots (2N per 1024-row block) and the Gram's row-slice partials grow with
+    # the rows and the members
+    assert _rows_ws(lib, 100000, 16)[1] > small
+    assert _rows_ws(lib, 1000, 64)[1] > small
+    assert _rows_ws(lib, 0, 16)[0] == SHAPE
+    assert _rows_ws(lib, 1000, 0)[0] == SHAPE
+    assert _rows_ws(lib, 1000, 1025)[0] == SHAPE
+    assert lib.enkf_rows_workspace(1000, 16, None) == ARG
+
+
+def _rows_level(lib, k=0, nobs=1000, nens=16, prec=FP32, r=A0, V=A1, ldv=None, D=A2, ldd=None, U=A3, ldu=None,
+                Z=A4, ldz=None, coef=A5, C=A0, gamma=A1, part=A2, ws=A3, wsb=None):
+    if wsb is None:
+        wsb = _rows_ws(lib, nobs, nens)[1]
+    return lib.enkf_rows_level(prec, nobs, nens, k, r, V, ldv or nobs, D, ldd or nobs, U, ldu or nobs, Z,
+                               ldz or nobs, coef, C, gamma, part, ws, wsb, None)
+
+
+def test_rows_level_rejects_bad_arguments(lib):
+    assert _rows_level(lib, prec=7) == ARG
+    assert _rows_level(lib, nens=0) == SHAPE
+    assert _rows_level(lib, k=-2) == ARG
+    assert _rows_level(lib, k=16) == ARG and "out of" in _err(lib)
+    assert _rows_level(lib, V=None) == ARG
+    assert _rows_level(lib, ws=None) == ARG
+    assert _rows_level(lib, k=3, part=None) == ARG              # the next level's dots are wanted
+    assert _rows_level(lib, k=-1, r=None) == ARG                # Step 1 needs r and D
+    assert _rows_level(lib, k=-1, D=None) == ARG
+    assert _rows_level(lib, k=0, coef=None) == ARG              # a level needs the reduced dots
+    assert _rows_level(lib, k=0, gamma=None) == ARG
+    assert _rows_level(lib, ldu=999) == SHAPE
+    assert _rows_level(lib, k=-1, ldd=999) == SHAPE
+    assert _rows_level(lib, wsb=64) == WS
+
+
+def test_rows_gram_assemble_xa_reject_bad_arguments(lib):
+    wsb = _rows_ws(lib, 1000, 16)[1]
+    assert lib.enkf_rows_gram(FP32, 1000, 16, A0, 1000, A1, 999, A2, A3, wsb, None) == SHAPE
+    assert lib.enkf_rows_gram(FP32, 1000, 16, A0, 1000, A1, 1000, None, A3, wsb, None) == ARG
+    assert lib.enkf_rows_gram(FP32, 1000, 16, A0, 1000, A1, 1000, A2, A3, 8, None) == WS
+    assert lib.enkf_rows_assemble(FP32, 1, A0, A1, A2, A3, None) == SHAPE     # M needs two members
+    assert lib.enkf_rows_assemble(FP64, 16, A0, None, A2, A3, None) == ARG
+    assert lib.enkf_rows_xa(FP32, 0, 16, A0, 1, A1, 1, A2, A3, 1, None) == SHAPE
+    assert lib.enkf_rows_xa(FP32, 500, 16, A0, 500, A1, 499, A2, A3, 500, None) == SHAPE
+    assert lib.enkf_rows_xa(FP32, 500, 16, A0, 500, None, 500, A2, A3, 500, None) == ARG
+    st = ctypes.c_int32(0)
+    assert lib.enkf_rows_status(None, None, ctypes.byref(st)) == ARG
+    assert lib.enkf_rows_status(A0, None, None) == ARG
