@@ -1,8 +1,9 @@
-"""Host-side argument checks of the entry points beside the analysis (inflation, partial
-localization, block-diagonal R, pivoted solve, the row-sharded analysis), run on the CPU: every
-call here is rejected by the library's validation before it touches the GPU, so placeholder
-device addresses (never dereferenced) stand in for arrays.  Also the workspace sizing of the
-pivoted solve and of the row-sharded analysis."""
+"""Host-side argument checks of the C ABI, run on the CPU: the analysis plan, the
+no-allocation solve, and the entry points beside the analysis (inflation, partial
+localization, block-diagonal R, pivoted solve, the row-sharded analysis).  Every call here is
+rejected by the library's validation before it touches the GPU, so placeholder device
+addresses (never dereferenced) stand in for arrays.  Also the workspace sizing of the pivoted
+solve and of the row-sharded analysis."""
 import ctypes
 import math
 
@@ -187,3 +188,41 @@ def test_rows_gram_assemble_xa_reject_bad_arguments(lib):
     st = ctypes.c_int32(0)
     assert lib.enkf_rows_status(None, None, ctypes.byref(st)) == ARG
     assert lib.enkf_rows_status(A0, None, None) == ARG
+
+
+# ---------------------------------------------------------------------------
+# The analysis plan: sizes, modes, widths and flags rejected before the device is touched.
+
+
+def test_plan_rejects_bad_sizes_widths_and_flags(lib):
+    h, ws = ctypes.c_void_p(), ctypes.c_size_t()
+
+    def plan(nstate=100, nobs=50, nens=8, mode=FP32, panel_b=0, flags=0, out=True, wsp=True):
+        return lib.enkf_ism_plan(ctypes.byref(h) if out else None, nstate, nobs, nens, mode, panel_b, flags,
+                                 ctypes.byref(ws) if wsp else None)
+
+    assert plan(out=False) == ARG
+    assert plan(wsp=False) == ARG
+    assert plan(nstate=0) == SHAPE and plan(nobs=0) == SHAPE and plan(nens=0) == SHAPE
+    assert plan(nens=1025) == SHAPE
+    assert plan(nobs=(1 << 40) + 1) == SHAPE
+    assert plan(mode=17) == ARG
+    # the single-problem panel width is at most 32 (the tensor-core kernel's shared-memory plan and
+    # its one-warp factor); 64 is refused, for every panel mode
+    for mode in (enkf.ENKF_PANEL_FP32, enkf.ENKF_PANEL_BF16, enkf.ENKF_PANEL_FP16, enkf.ENKF_PANEL_BF16X3):
+        assert plan(mode=mode, panel_b=64) == ARG and "panel_b" in _err(lib)
+        assert plan(mode=mode, panel_b=33) == ARG
+        assert plan(mode=mode, panel_b=-1) == ARG
+    assert plan(flags=0x100) == ARG and "flag" in _err(lib)
+
+
+def test_noalloc_solve_rejects_bad_arguments(lib):
+    def call(nobs=1000, nens=16, prec=FP32, r=A0, V=A1, ldv=None, D=A2, ldd=None, Z=A3, ldz=None):
+        return lib.enkf_ism_solve_noalloc(nobs, nens, prec, r, V, ldv or nobs, D, ldd or nobs, Z, ldz or nobs,
+                                          None, None)
+
+    assert call(r=None) == ARG and call(Z=None) == ARG
+    assert call(prec=enkf.ENKF_PANEL_FP32) == ARG            # the plain FP64 / FP32 solve only
+    assert call(nobs=0) == SHAPE and call(nens=1025) == SHAPE
+    assert call(ldz=999) == SHAPE and call(ldv=999) == SHAPE
+    assert call(prec=FP64, D=ctypes.c_void_p(0x300000004)) == ARG and "aligned" in _err(lib)
