@@ -226,3 +226,83 @@ def test_noalloc_solve_rejects_bad_arguments(lib):
     assert call(nobs=0) == SHAPE and call(nens=1025) == SHAPE
     assert call(ldz=999) == SHAPE and call(ldv=999) == SHAPE
     assert call(prec=FP64, D=ctypes.c_void_p(0x300000004)) == ARG and "aligned" in _err(lib)
+
+
+# ---------------------------------------------------------------------------
+# The forecast (RK4 and the surrogate), the surrogate's training entry points and the batch plan.
+
+UNSUP = enkf.ENKF_ERR_UNSUPPORTED
+RK4, SURR = enkf.ENKF_FORECAST_RK4, enkf.ENKF_FORECAST_SURROGATE
+
+
+def test_forecast_workspace_sizes(lib):
+    b = ctypes.c_size_t(7)
+    assert lib.enkf_forecast_workspace(4096, 256, RK4, ctypes.byref(b)) == enkf.ENKF_OK and b.value == 0
+    assert lib.enkf_forecast_workspace(4096, 256, SURR, ctypes.byref(b)) == enkf.ENKF_OK and b.value > 0
+    small = b.value
+    assert lib.enkf_forecast_workspace(4096, 512, SURR, ctypes.byref(b)) == enkf.ENKF_OK and b.value > small
+    assert lib.enkf_forecast_workspace(4096, 256, 9, ctypes.byref(b)) == UNSUP
+    assert lib.enkf_forecast_workspace(0, 256, RK4, ctypes.byref(b)) == SHAPE
+    assert lib.enkf_forecast_workspace(4096, 256, RK4, None) == ARG
+
+
+def test_forecast_rejects_bad_arguments(lib):
+    def call(X=A0, ld=None, nstate=40, nens=20, prec=FP64, nsteps=5, method=RK4, weights=None, ws=None, wsb=0):
+        return lib.enkf_forecast(X, ld or nstate, nstate, nens, prec, 8.0, 0.01, nsteps, method, weights, ws, wsb,
+                                 None)
+
+    assert call(X=None) == ARG
+    assert call(prec=enkf.ENKF_PANEL_BF16) == ARG
+    assert call(nstate=3) == SHAPE and call(ld=39) == SHAPE and call(nsteps=-1) == SHAPE
+    assert call(X=ctypes.c_void_p(0x100000004)) == ARG           # FP64 state not 8-byte aligned
+    assert call(nstate=6145) == SHAPE                             # the RK4 state lives in shared memory
+    assert call(nsteps=0) == enkf.ENKF_OK                         # nothing to do, nothing launched
+    assert call(method=SURR) == UNSUP                             # the surrogate runs on FP32 states
+    assert call(method=SURR, prec=FP32) == ARG                    # no weights
+    assert call(method=SURR, prec=FP32, weights=A1, ws=A2, wsb=16) == WS
+    assert call(method=3, prec=FP32) == UNSUP
+
+
+def test_surrogate_entry_points_reject_bad_arguments(lib):
+    n, pb, wb = ctypes.c_int64(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.enkf_surrogate_sizes(4096, 64, ctypes.byref(n), ctypes.byref(pb), ctypes.byref(wb)) == enkf.ENKF_OK
+    assert n.value > 0 and pb.value > 0 and wb.value > 0
+    assert lib.enkf_surrogate_sizes(4, 64, None, None, None) == SHAPE
+    assert lib.enkf_surrogate_sizes(4096, 0, None, None, None) == SHAPE
+    assert lib.enkf_surrogate_pack(None, A1, None) == ARG
+    assert lib.enkf_surrogate_pack(A0, ctypes.c_void_p(0x200000010), None) == ARG   # packed not 256-byte aligned
+
+    def train(master=A0, m=A1, v=A2, step=1, packed=A3, X=A4, target=A5, nstate=4096, nbatch=64, ws=A0,
+              wsb=None, sq=A1):
+        return lib.enkf_surrogate_train_step(master, m, v, step, 1e-3, packed, X, target, nstate, nbatch, ws,
+                                             wb.value if wsb is None else wsb, sq, None, None)
+
+    assert train(master=None) == ARG and train(sq=None) == ARG
+    assert train(m=None) == ARG                                   # Adam's moments from step 1 on
+    assert train(nstate=4) == SHAPE and train(nbatch=0) == SHAPE
+    assert train(wsb=16) == WS and train(ws=None) == WS
+
+
+def test_batch_plan_rejects_bad_problems(lib):
+    P = enkf.enkf_ism_problem
+    h, ws = ctypes.c_void_p(), ctypes.c_size_t()
+
+    def plan(probs, mode=FP32, flags=0, n=None):
+        arr = (P * max(1, len(probs)))(*probs)
+        return lib.enkf_ism_batch_plan(ctypes.byref(h), len(probs) if n is None else n, arr, mode, flags,
+                                       ctypes.byref(ws))
+
+    def prob(nobs=100, nens=32, ldv=None, ldd=None, Z=0, ldz=None, r=0):
+        return P(nobs=nobs, nens=nens, reserved=0, r=r, V=0, D=0, ldv=ldv or nobs, ldd=ldd or nobs, Z=Z,
+                 ldz=ldz or nobs, M=-1)
+
+    assert lib.enkf_ism_batch_plan(None, 0, None, FP32, 0, ctypes.byref(ws)) == ARG
+    assert plan([prob()], n=-1) == SHAPE
+    assert plan([prob()], mode=FP64) == UNSUP                     # the batched kernel is built for FP32
+    assert plan([prob()], flags=enkf.ENKF_FLAG_REFINE) == ARG
+    assert plan([prob(), prob(nens=30)]) == SHAPE and "problem 1" in _err(lib)   # nens a multiple of 4
+    assert plan([prob(nens=132)]) == SHAPE
+    assert plan([prob(nobs=0)]) == SHAPE
+    assert plan([prob(ldd=99)]) == SHAPE
+    assert plan([prob(ldz=99)]) == SHAPE
+    assert plan([prob(r=-8)]) == ARG
